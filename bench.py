@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Throughput of the culled forward + backward of an N-dimensional Gaussian
+mixture (the fit step of "N-Dimensional Gaussians for Fitting of High
+Dimensional Functions"), in Gaussian-query pairs per second.
+
+Workload (synthetic, seeded): N = 6, 100,000 Gaussians (each with a child
+of negligible brightness, the state after the first refinement), 2^20
+queries uniform in [-1, 1]^6 in Morton-ordered tiles of 256, 16 random
+projections, contribution cutoff 1/255.  One step = cull + forward + L2 loss
++ backward + Adam + refinement check, all in libndg's kernels.  Pairs per
+step = sum over tiles of (queries in tile x candidates in tile).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  With --gpus N > 1 (under torchrun) every rank
+fits its own independent replica (no collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "culled fwd+bwd Gaussian-query pairs/s and N=10 1080p render ms, vs plain FP32"
+UNIT = "pairs/s"
+N_DIM, G, Q, K_PROJ, TILE, BUCKETS = 6, 100_000, 1 << 20, 16, 256, 64
+CUTOFF = 1.0 / 255.0
+WORKLOAD = (f"N={N_DIM} culled fit step: {G} Gaussians (+{G} children at brightness t/10), "
+            f"Q=2^20 Morton-tiled queries, tile {TILE}, k={K_PROJ} projections, "
+            f"cutoff 1/255, {BUCKETS} buckets, Adam lr 1e-3")
+
+
+def flops_per_pair(N: int):
+    """Algorithmic FP32 flops per Gaussian-query pair (FMA = 2):
+    forward  d = x - m (N), z = M d (N(N+1)), s = |z|^2 (2N), scale (1),
+             w e (6)                                 -> N^2 + 4N + 7
+    backward the forward's N^2 + 4N + 1 again, sum dy e (6), beta (6),
+             beta z (N), sum beta z (N), sum beta z d^T (N(N+1))
+                                                     -> 2N^2 + 7N + 13."""
+    return N * N + 4 * N + 7, 2 * N * N + 7 * N + 13
+
+
+def fp32_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
+    """FP32 FMA pipe: 128 lanes x 2 flops per SM per clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, reasons) while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        mhz, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx or None,
+                "samples": len(mhz), "reasons": sorted(reasons)}
+
+
+def build_workload(device):
+    import torch
+    from paper_2405_20067_gb300 import ndg, synth
+    c = synth.config1()
+    mix = c["mix"]
+    ch = synth.children(N_DIM, G, 11, spread=0.05, brightness=(0.0009, 0.0011))
+    gm = ndg.Mixture.from_arrays(N_DIM, mix, ch, G_cap=G + G // 10, device=device)
+    x = torch.as_tensor(c["x"]).to(device)
+    target = torch.as_tensor(c["target"]).to(device)
+    proj = torch.as_tensor(c["proj"]).to(device)
+    cp = ndg.CullParams(K_PROJ, proj, CUTOFF, 3.0, BUCKETS)
+    return c, ch, gm, x, target, cp
+
+
+def pairs_of(cull, Qn, tile):
+    import torch
+    offs = cull.offsets
+    cnt = offs[1:] - offs[:-1]
+    T = cnt.shape[0]
+    qt = torch.full((T,), tile, dtype=torch.int64, device=offs.device)
+    if T:
+        qt[-1] = Qn - tile * (T - 1)
+    return int((cnt * qt).sum().item())
+
+
+def cpu_baseline(c, ch, seconds: float = 15.0):
+    """The FP64 oracle on a bounded sample of the same workload: culled
+    forward + L2 loss + gradient on a subset of tiles (host cores)."""
+    import oracle
+    from paper_2405_20067_gb300 import synth  # noqa: F401  (inputs only)
+    oracle.build()
+    names = ["mean", "theta", "alpha_raw", "color_raw", "u_theta", "m_u", "c_alpha_raw",
+             "c_color_raw"]
+    raw = oracle.Raw.from_arrays([c["mix"][n] for n in names[:4]] + [ch[n] for n in names[4:]], True)
+    x = c["x"].astype(np.float64)
+    L, m, w = oracle.activate(raw)
+    offs, ids = oracle.cull_contract(L, m, w, x, TILE, c["proj"], CUTOFF, 3.0, BUCKETS)
+    T = len(offs) - 1
+    rng = np.random.default_rng(0)
+    order = rng.permutation(T)
+
+    def run(ntiles):
+        sel = np.sort(order[:ntiles])
+        xs = np.concatenate([x[t * TILE:(t + 1) * TILE] for t in sel])
+        ts = np.concatenate([c["target"][t * TILE:(t + 1) * TILE] for t in sel]).astype(np.float64)
+        so = np.zeros(ntiles + 1, np.int64)
+        lists = [ids[offs[t]:offs[t + 1]] for t in sel]
+        so[1:] = np.cumsum([len(l) for l in lists])
+        si = np.concatenate(lists).astype(np.int32) if lists else np.zeros(0, np.int32)
+        pairs = int(sum(len(l) for l in lists) * TILE)
+        t0 = time.perf_counter()
+        La, ma, wa = oracle.activate(raw)
+        y = oracle.eval(La, ma, wa, xs, TILE, so, si)
+        _, gbar = oracle.loss_l2(y, ts)
+        oracle.grad(raw, xs, TILE, so, si, gbar)
+        return pairs, time.perf_counter() - t0
+
+    p1, t1 = run(4)
+    n = int(min(T, max(4, 4 * seconds / max(t1, 1e-3))))
+    p, t = run(n)
+    return {"value": p / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} of {T} tiles ({p:.3g} pairs), FP64 culled forward + loss + gradient",
+            "seconds": round(t, 2)}
+
+
+def run_reference(args):
+    """The oracle as it stands, timed on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2405_20067_gb300 import synth
+    c = synth.config1()
+    ch = synth.children(N_DIM, G, 11, spread=0.05, brightness=(0.0009, 0.0011))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(c, ch, seconds=5.0)
+        if i >= args.warmup:
+            vals.append(cb)
+    v = statistics.median([cb["value"] for cb in vals])
+    cb = dict(vals[-1])
+    cb["value"] = v
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
+           "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(device))
+    from paper_2405_20067_gb300 import build, ndg
+    from paper_2405_20067_gb300.train import Trainer
+    build.build()
+    peaks, peak_kind = load_peaks()
+    c, ch, gm, x, target, cp = build_workload(device)
+    tr = Trainer(gm, x, target, TILE, cp, lr=1e-3, t=0.01, phase=0)
+    names = ["build_cull", "forward", "loss", "backward", "adam", "densify"]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)  # > 129 MB L2
+
+    def one_step(traces):
+        tr.set_traces(traces)
+        tr.step(refine=False)
+        tr.refine(sync=False)
+
+    for _ in range(args.warmup):
+        one_step(None)
+    torch.cuda.synchronize()
+    tr.check()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    traces = [{n: ndg.Trace() for n in names} for _ in range(args.steps)]
+    pairs = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record()
+            one_step(traces[i])
+            ends[i].record()
+            pairs.append(tr.ev.cull)  # counted after the timed region
+            torch.cuda.synchronize()
+            pairs[-1] = pairs_of(tr.ev.cull, Q, TILE)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    st = tr.check()
+    assert st == ndg.NDG_OK, ndg.status_string(st)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    total_pairs = sum(pairs) * world
+    value = total_pairs / (total_ms / 1e3)
+    kern = {n: statistics.mean(tr_[n].ms() for tr_ in traces) for n in names}
+    launches = sum(tr_[n].launches for tr_ in traces for n in names)
+    fwd_f, bwd_f = flops_per_pair(N_DIM)
+    mean_pairs = statistics.mean(pairs)
+    clocks = clk.summary()
+    peak_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = fp32_peak_tflops(peak_mhz)
+    achieved = mean_pairs * bwd_f / (kern["backward"] / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": "bwd_kernel<6> (per-pair partials)",
+                "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz "
+                               f"(clock from {peak_kind} peaks file)"}
+    kernels = {n: {"ms": round(kern[n], 4)} for n in names}
+    kernels["forward"]["tflops"] = round(mean_pairs * fwd_f / (kern["forward"] / 1e3) / 1e12, 3)
+    kernels["backward"]["tflops"] = round(achieved, 3)
+
+    # end to end through the public API: host inputs copied in, loss read out
+    xh = x.cpu().pin_memory()
+    th = target.cpu().pin_memory()
+    e2e_ms = []
+    for i in range(max(3, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss = tr.step(xh, th, refine=False)
+        tr.refine(sync=False)
+        float(loss.item())
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_ms = e2e_ms[1:]
+    e2e = {"value": mean_pairs / (statistics.mean(e2e_ms) / 1e3) * world, "unit": UNIT,
+           "h2d_bytes_per_step": int(xh.numel() * 4 + th.numel() * 4), "d2h_bytes_per_step": 8}
+    if rank != 0:
+        return
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "pairs_per_step": mean_pairs,
+                      "candidates_per_step": int(tr.ev.cull.E()),
+                      "l2": "256 MB buffer written between timed steps (untimed)",
+                      "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
+           "roofline": roofline, "kernels_ms": kernels, "gpu_launches": launches,
+           "e2e": e2e, "clocks": clocks}
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(c, ch)
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * ndg.h -- C ABI of libndg: evaluation, culling, back-propagation and
+ * refinement of mixtures of N-dimensional Gaussians on one GB300 (sm_103a).
+ *
+ * Method: "N-Dimensional Gaussians for Fitting of High Dimensional
+ * Functions" (SIGGRAPH 2024).  Each Gaussian has a mean m, a lower
+ * triangular covariance factor L (V = L L^T, Section 3.1 Eq. 2) and an RGB
+ * weight w = alpha c (Section 4.1 Eq. 8); the mixture value at a query x is
+ *     y(x) = sum_g w_g exp(-1/2 (x - m_g)^T V_g^{-1} (x - m_g))   (Eq. 1, 8)
+ * restricted, per tile of consecutive queries, to the Gaussians that survive
+ * the random-projection cull of Section 3.2 (Eq. 3-5).
+ *
+ * Conventions shared by every entry point
+ *   - Every pointer is caller-owned DEVICE memory unless stated otherwise;
+ *     the library never allocates or frees memory and keeps no global
+ *     state.  Float arrays are FP32, row-major, contiguous, 4-byte aligned.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
+ *     default stream).  Argument errors are detected on the host and
+ *     returned before anything is launched.  Errors found on the device
+ *     (capacity overflow, non-finite parameters) are written to a status
+ *     word inside the workspace and read with ndg_read_status().
+ *   - `ws` is scratch device memory of at least ndg_workspace_size() bytes
+ *     (256-byte aligned).  Calls that share a workspace must be ordered on
+ *     one stream.
+ *   - Raw parameters (per parent row g, G rows in use, G_cap allocated):
+ *       mean      [G_cap][N]
+ *       theta     [G_cap][P]  P = N(N+1)/2, packed lower triangle row by
+ *                             row: entry (i,j), j <= i, at i(i+1)/2 + j.
+ *                             L_ii = exp(theta), L_ij = 2 sigmoid(theta) - 1
+ *                             (Section 3.1; the paper's "i<j" read as the
+ *                             strictly lower entries)
+ *       alpha_raw [G_cap]     brightness alpha = exp(a)      (Section 4.1)
+ *       color_raw [G_cap][3]  colour c = sigmoid(gamma)      (Section 4.1)
+ *     and, when has_children != 0, one child per parent (Section 3.3,
+ *     Eq. 6-7: L_c = L_p U, m_c = L_p m_u + m_p), same shapes:
+ *       u_theta [G_cap][P], m_u [G_cap][N], c_alpha_raw [G_cap],
+ *       c_color_raw [G_cap][3].
+ *     Evaluated Gaussians: Ge = G (1 + has_children); index e < G is parent
+ *     e, index e >= G is the child of parent e - G.
+ *   - Queries: Q points x [Q][N]; tile t holds queries
+ *     [t tile_size, min(Q, (t+1) tile_size)), T = ceil(Q / tile_size).
+ *     Tiles are the unit of culling (Section 3.2: 16 x 16 pixel tiles), so
+ *     consecutive queries should be close (image tiles, Morton order).
+ */
+#ifndef NDG_H
+#define NDG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NDG_OK = 0,
+  NDG_ERR_INVALID_ARG = 1, /* bad size, NULL or misaligned pointer       */
+  NDG_ERR_CAPACITY = 2,    /* candidate entries exceeded E_cap           */
+  NDG_ERR_CUDA = 3,        /* a CUDA launch or copy failed               */
+  NDG_ERR_NUMERIC = 4,     /* non-finite value in the parameters         */
+  NDG_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out         */
+  NDG_ERR_WORKSPACE = 6    /* ws smaller than ndg_workspace_size()       */
+} ndg_status;
+
+#define NDG_MAX_N 12      /* dimensions                                  */
+#define NDG_MAX_K 32      /* random projections                          */
+#define NDG_MAX_BUCKETS 255
+#define NDG_MAX_TILE 256  /* queries per tile                            */
+
+typedef void* ndg_stream; /* a cudaStream_t */
+
+/* Raw mixture parameters (layouts above).  The same struct describes
+ * gradients and Adam moments, which share the parameters' layout. */
+typedef struct {
+  int N, G, G_cap, has_children;
+  float *mean, *theta, *alpha_raw, *color_raw;
+  float *u_theta, *m_u, *c_alpha_raw, *c_color_raw;
+} ndg_mixture;
+
+typedef struct {
+  long long Q;      /* number of queries (>= 0)                           */
+  int tile_size;    /* 1 .. NDG_MAX_TILE                                  */
+  const float* x;   /* [Q][N] device                                      */
+} ndg_queries;
+
+/* Section 3.2: k random unit vectors r_j (rows of proj, [k][N] device).  A
+ * Gaussian is dropped for a tile when, for some j, the tile's projected
+ * queries lie outside m_r +- k_g sigma_r (Eq. 3-5, "outside" per the text
+ * around Eq. 5).  k_g = k_sigma (the paper uses 3) when cutoff == 0;
+ * with cutoff > 0, k_g = sqrt(2 ln(max_c w_gc / cutoff)) so that every
+ * dropped contribution is below cutoff, and a Gaussian whose largest weight
+ * is below cutoff is dropped everywhere.  k == 0 keeps every live Gaussian
+ * in every tile (dense evaluation).  The decision follows an integer bucket
+ * contract over `buckets` (1 .. NDG_MAX_BUCKETS) buckets per projection
+ * that is reproducible bit for bit and never drops a pair the real-valued
+ * test keeps. */
+typedef struct {
+  int k;
+  const float* proj;
+  float cutoff;
+  float k_sigma;
+  int buckets;
+} ndg_cull_params;
+
+/* Candidate lists as CSR over tiles.  Caller-owned device buffers:
+ * offsets [T+1] (int64), ids [E_cap] (int32 evaluated-Gaussian indices),
+ * E_dev [1] (int64, the true total, which may exceed E_cap).  Offsets are
+ * clamped to E_cap, so a truncated list never indexes past the buffer. */
+typedef struct {
+  long long* offsets;
+  int* ids;
+  long long E_cap;
+  long long* E_dev;
+} ndg_cull;
+
+/* Optional per-call trace (every entry point that launches work takes one;
+ * NULL disables it).  main_begin / main_end are cudaEvent_t handles (or
+ * NULL) recorded on the call's stream immediately before and after its main
+ * kernel: the per-tile cull (fill pass) of ndg_build_cull, the evaluation
+ * of ndg_forward, the per-pair partials of ndg_backward, the update of
+ * ndg_adam, the selection of ndg_densify, the reduction of ndg_loss_l2.
+ * `launches` is increased by the number of kernels the call launched. */
+typedef struct {
+  void* main_begin;
+  void* main_end;
+  long long launches;
+} ndg_trace;
+
+/* Bytes of workspace needed by every call below for these sizes.
+ * E_cap bounds the candidate entries ndg_backward may see. */
+size_t ndg_workspace_size(const ndg_mixture* mix, const ndg_queries* q,
+                          const ndg_cull_params* cp, long long E_cap);
+
+/* Section 3.2 (Eq. 3-5): build the per-tile candidate lists.  Order inside
+ * a tile is deterministic (by first-projection bucket range, then index).
+ * Device errors: NDG_ERR_CAPACITY when more than E_cap entries exist (the
+ * lists are truncated, *E_dev holds the true total). */
+ndg_status ndg_build_cull(const ndg_mixture* mix, const ndg_queries* q,
+                          const ndg_cull_params* cp, ndg_cull* out, void* ws,
+                          size_t ws_bytes, ndg_stream stream, ndg_trace* trace);
+
+#define NDG_MODE_FP32 0 /* centred form z = L^{-1}(x - m) on the FP32 pipe */
+
+/* Eq. 1 and Eq. 8: y [Q][3] = culled mixture sum at every query.  `cull`
+ * must come from ndg_build_cull on the same mixture and queries. */
+ndg_status ndg_forward(const ndg_mixture* mix, const ndg_queries* q,
+                       const ndg_cull* cull, int mode, float* y, void* ws,
+                       size_t ws_bytes, ndg_stream stream, ndg_trace* trace);
+
+/* Plain L2 loss over the Q x 3 outputs (the paper trains with a relative L2,
+ * Section 4.1; the plain form is the one used here):
+ *   loss = sum (y - target)^2 / (3Q) written to loss_dev [1] (FP64),
+ *   dy = 2 (y - target) / (3Q)  [Q][3].  Deterministic reduction. */
+ndg_status ndg_loss_l2(long long Q, const float* y, const float* target,
+                       float* dy, double* loss_dev, void* ws, size_t ws_bytes,
+                       ndg_stream stream, ndg_trace* trace);
+
+/* Analytic gradient of the loss through Eq. 1, 2, 6-8 given dy = dl/dy
+ * [Q][3]: writes dl/d(raw parameter) into `grad` (same layout and N, G,
+ * has_children as mix; rows >= G untouched).  Recomputes everything from
+ * the raw parameters and `cull`; per-Gaussian sums run in a fixed order
+ * (no atomics), so results are bit-reproducible.  Requires E < 2^31. */
+ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q,
+                        const ndg_cull* cull, const float* dy,
+                        ndg_mixture* grad, void* ws, size_t ws_bytes,
+                        ndg_stream stream, ndg_trace* trace);
+
+/* Adam (Kingma & Ba) over every raw parameter of rows < G (children too
+ * when has_children); the paper does not name its optimiser.  m1, m2 are
+ * the first and second moments in the parameters' layout; step_dev [1] is
+ * the device step counter t (read as t, the update uses t + 1, then it is
+ * incremented), so the call can be captured in a CUDA graph. */
+ndg_status ndg_adam(ndg_mixture* params, const ndg_mixture* grad,
+                    ndg_mixture* m1, ndg_mixture* m2, int* step_dev, float lr,
+                    float beta1, float beta2, float eps, ndg_stream stream,
+                    ndg_trace* trace);
+
+/* Section 3.3 refinement.  Children whose raw brightness exceeds
+ * a_thr = (float) ln t materialise as new parents appended at rows
+ * G .. G_new-1 (L = L_p U written back to raw form with off-diagonals
+ * clamped to +-(1 - 1e-6), m = L_p m_u + m_p, the child's own brightness
+ * and colour); at most G_cap - G do, the brightest first, ties at the
+ * boundary all left out.  Every materialised parent and new row receives a
+ * fresh child from its row of `noise` [G_cap][P + N + 4] (standard
+ * normals): u_theta = 0.05 xi, m_u = 0.1 xi, c_alpha_raw = a_child0 +
+ * 0.1 xi, c_color_raw = own colour + 0.1 xi; Adam moments of every touched
+ * row are zeroed.  With has_children == 0 every parent receives a child and
+ * nothing materialises.  G_new_dev [1] receives the new row count; the
+ * caller sets mix->G and has_children = 1 for later calls. */
+ndg_status ndg_densify(ndg_mixture* mix, float a_thr, float a_child0,
+                       const float* noise, ndg_mixture* m1, ndg_mixture* m2,
+                       int* G_new_dev, void* ws, size_t ws_bytes,
+                       ndg_stream stream, ndg_trace* trace);
+
+/* Synchronises `stream`, copies the workspace status word to *device_status
+ * (an ndg_status value) and clears it. */
+ndg_status ndg_read_status(void* ws, ndg_stream stream, int* device_status);
+
+const char* ndg_status_string(int status);
+int ndg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NDG_H */

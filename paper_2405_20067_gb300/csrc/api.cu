@@ -1,0 +1,541 @@
+// api.cu -- the C ABI declared in include/ndg.h: argument checks, the
+// workspace layout and the launch sequence of every entry point.
+//
+// Workspace layout (256-byte aligned regions).  A common part that every
+// call may use, followed by ONE of two call-specific parts that start at the
+// same offset (calls sharing a workspace are ordered on one stream, and the
+// call-specific parts only hold temporaries of the call that owns them):
+//   common : header (status word), loss partial sums, prepared records
+//            [2 G_cap][R], densify scratch (flag, rank, fresh: [G_cap] each)
+//   cull   : per-tile projection bounds and bucket keys, per-Gaussian bucket
+//            keys and bins, the bin sort's buffers and offsets, per-tile
+//            counts and their scan, sort / scan temporaries
+//   bwd    : per-entry partial records [E_cap][RP], the transposition sort's
+//            buffers, per-Gaussian offsets and sums, sort temporaries
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "common.cuh"
+#include "internal.h"
+#include "kernels.h"
+
+using namespace ndg;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t kLossParts = 512;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Region {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t r = off;
+    off += align_up(bytes ? bytes : 1);
+    return r;
+  }
+};
+
+struct Sizes {
+  int N = 0, G_cap = 0, Ge_cap = 0, tile = 1, k = 0, KP = 0, B = 1;
+  long long Q = 0, T = 0, E_cap = 0;
+};
+
+struct CommonLayout {
+  size_t header, rec, loss, dflag, drank, dfresh, end;
+};
+struct CullLayout {
+  size_t tb, range, tkey, gkey, bin, bk_a, bv_a, bk_b, bv_b, binoff, counts, excl, tmp, end;
+};
+struct BwdLayout {
+  size_t part, sk_a, sv_a, sk_b, sv_b, goff, gsum, tmp, end;
+};
+
+CommonLayout common_layout(const Sizes& z) {
+  Region r;
+  CommonLayout c;
+  c.header = r.take(sizeof(WsHeader));
+  c.loss = r.take(kLossParts * sizeof(double));  // fixed offset: ndg_loss_l2 knows no sizes
+  c.rec = r.take((size_t)z.Ge_cap * rec_floats(z.N) * sizeof(float));
+  c.dflag = r.take((size_t)z.G_cap * sizeof(int));
+  c.drank = r.take((size_t)z.G_cap * sizeof(int));
+  c.dfresh = r.take((size_t)z.G_cap * sizeof(int));
+  c.end = r.off;
+  return c;
+}
+
+CullLayout cull_layout(const Sizes& z, size_t base) {
+  Region r;
+  r.off = base;
+  CullLayout c;
+  const int nb = z.k > 0 ? z.B : 1;
+  c.tb = r.take((size_t)z.T * z.k * 2 * sizeof(float));
+  c.range = r.take(3 * NDG_MAX_K * sizeof(float));
+  c.tkey = r.take((size_t)z.T * 2 * z.KP);
+  c.gkey = r.take((size_t)z.Ge_cap * 2 * z.KP);
+  c.bin = r.take((size_t)z.Ge_cap * 4);
+  c.bk_a = r.take((size_t)z.Ge_cap * 4);
+  c.bv_a = r.take((size_t)z.Ge_cap * 4);
+  c.bk_b = r.take((size_t)z.Ge_cap * 4);
+  c.bv_b = r.take((size_t)z.Ge_cap * 4);
+  c.binoff = r.take(((size_t)nb * nb + 1) * sizeof(long long));
+  c.counts = r.take((size_t)(z.T + 1) * sizeof(long long));
+  c.excl = r.take((size_t)(z.T + 1) * sizeof(long long));
+  size_t t1 = radix_temp_bytes(z.Ge_cap), t2 = scan_temp_bytes(z.T + 1);
+  c.tmp = r.take(t1 > t2 ? t1 : t2);
+  c.end = r.off;
+  return c;
+}
+
+BwdLayout bwd_layout(const Sizes& z, size_t base) {
+  Region r;
+  r.off = base;
+  BwdLayout b;
+  b.part = r.take((size_t)z.E_cap * part_floats(z.N) * sizeof(float));
+  b.sk_a = r.take((size_t)z.E_cap * 4);
+  b.sv_a = r.take((size_t)z.E_cap * 4);
+  b.sk_b = r.take((size_t)z.E_cap * 4);
+  b.sv_b = r.take((size_t)z.E_cap * 4);
+  b.goff = r.take(((size_t)z.Ge_cap + 1) * sizeof(long long));
+  b.gsum = r.take((size_t)z.Ge_cap * part_floats(z.N) * sizeof(float));
+  b.tmp = r.take(radix_temp_bytes(z.E_cap));
+  b.end = r.off;
+  return b;
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+ndg_status check_mix(const ndg_mixture* m) {
+  if (!m) return NDG_ERR_INVALID_ARG;
+  if (m->N < 1 || m->N > NDG_MAX_N || m->G < 0 || m->G_cap < m->G) return NDG_ERR_INVALID_ARG;
+  if (m->G > (1 << 30)) return NDG_ERR_INVALID_ARG;
+  if (m->G > 0) {
+    const float* need[4] = {m->mean, m->theta, m->alpha_raw, m->color_raw};
+    for (const float* p : need)
+      if (!p || !aligned(p, 4)) return NDG_ERR_INVALID_ARG;
+    if (m->has_children) {
+      const float* ch[4] = {m->u_theta, m->m_u, m->c_alpha_raw, m->c_color_raw};
+      for (const float* p : ch)
+        if (!p || !aligned(p, 4)) return NDG_ERR_INVALID_ARG;
+    }
+  }
+  return NDG_OK;
+}
+
+ndg_status check_queries(const ndg_queries* q) {
+  if (!q || q->Q < 0 || q->tile_size < 1 || q->tile_size > NDG_MAX_TILE) return NDG_ERR_INVALID_ARG;
+  if (q->Q > 0 && (!q->x || !aligned(q->x, 4))) return NDG_ERR_INVALID_ARG;
+  return NDG_OK;
+}
+
+ndg_status check_cull_params(const ndg_cull_params* cp) {
+  if (!cp || cp->k < 0 || cp->k > NDG_MAX_K) return NDG_ERR_INVALID_ARG;
+  if (cp->k > 0 && !cp->proj) return NDG_ERR_INVALID_ARG;
+  if (cp->buckets < 1 || cp->buckets > NDG_MAX_BUCKETS) return NDG_ERR_INVALID_ARG;
+  if (!(cp->cutoff >= 0.0f) || !std::isfinite(cp->cutoff)) return NDG_ERR_INVALID_ARG;
+  if (!(cp->cutoff > 0.0f) && !(cp->k_sigma >= 0.0f)) return NDG_ERR_INVALID_ARG;
+  return NDG_OK;
+}
+
+ndg_status check_cull(const ndg_cull* c) {
+  if (!c || !c->offsets || !c->E_dev || c->E_cap < 0) return NDG_ERR_INVALID_ARG;
+  if (c->E_cap > 0 && !c->ids) return NDG_ERR_INVALID_ARG;
+  return NDG_OK;
+}
+
+Sizes make_sizes(const ndg_mixture* m, const ndg_queries* q, const ndg_cull_params* cp,
+                 long long E_cap) {
+  Sizes z;
+  z.N = m->N;
+  z.G_cap = m->G_cap;
+  z.Ge_cap = 2 * m->G_cap;
+  z.Q = q ? q->Q : 0;
+  z.tile = q ? q->tile_size : 1;
+  z.T = q ? (z.Q + z.tile - 1) / z.tile : 0;
+  z.k = cp ? cp->k : 0;
+  z.KP = key_pad(z.k);
+  z.B = cp ? cp->buckets : 1;
+  z.E_cap = E_cap;
+  return z;
+}
+
+int bits_for(long long n_values) {  // bits to hold values 0 .. n_values - 1
+  int b = 1;
+  while (b < 40 && (1ll << b) < n_values) ++b;
+  return b;
+}
+
+ndg_status cuda_ok() {
+  return cudaGetLastError() == cudaSuccess ? NDG_OK : NDG_ERR_CUDA;
+}
+
+__global__ void finalize_offsets_kernel(const long long* __restrict__ excl, long long T,
+                                        long long E_cap, long long* __restrict__ offsets,
+                                        long long* __restrict__ E_dev, int* status) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t > T) return;
+  long long v = excl[t];
+  offsets[t] = v < E_cap ? v : E_cap;
+  if (t == T) {
+    *E_dev = v;
+    if (v > E_cap) set_status(status, NDG_ERR_CAPACITY);
+  }
+}
+
+// Counts launches and records the trace events around the main kernel.
+struct Tracer {
+  ndg_trace* t;
+  cudaStream_t s;
+  long long n = 0;
+  Tracer(ndg_trace* t_, cudaStream_t s_) : t(t_), s(s_) {}
+  void begin() {
+    if (t && t->main_begin) cudaEventRecord((cudaEvent_t)t->main_begin, s);
+  }
+  void end() {
+    if (t && t->main_end) cudaEventRecord((cudaEvent_t)t->main_end, s);
+  }
+  Tracer& operator+=(int k) {
+    n += k;
+    return *this;
+  }
+  ~Tracer() {
+    if (t) t->launches += n;
+  }
+};
+
+PrepArgs prep_args(const ndg_mixture* m) {
+  PrepArgs a{};
+  a.G = m->G;
+  a.Ge = m->has_children ? 2 * m->G : m->G;
+  a.mean = m->mean;
+  a.theta = m->theta;
+  a.alpha_raw = m->alpha_raw;
+  a.color_raw = m->color_raw;
+  a.u_theta = m->u_theta;
+  a.m_u = m->m_u;
+  a.c_alpha_raw = m->c_alpha_raw;
+  a.c_color_raw = m->c_color_raw;
+  return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ndg_workspace_size(const ndg_mixture* mix, const ndg_queries* q,
+                          const ndg_cull_params* cp, long long E_cap) {
+  if (!mix || mix->N < 1 || mix->N > NDG_MAX_N || mix->G_cap < 0) return 0;
+  Sizes z = make_sizes(mix, q, cp, E_cap < 0 ? 0 : E_cap);
+  CommonLayout c = common_layout(z);
+  size_t need = c.end;
+  if (cp) {
+    CullLayout cl = cull_layout(z, c.end);
+    need = cl.end > need ? cl.end : need;
+  }
+  if (E_cap > 0) {
+    BwdLayout bl = bwd_layout(z, c.end);
+    need = bl.end > need ? bl.end : need;
+  }
+  return need;
+}
+
+ndg_status ndg_build_cull(const ndg_mixture* mix, const ndg_queries* q, const ndg_cull_params* cp,
+                          ndg_cull* out, void* ws, size_t ws_bytes, ndg_stream stream,
+                          ndg_trace* trace) {
+  ndg_status st;
+  if ((st = check_mix(mix)) || (st = check_queries(q)) || (st = check_cull_params(cp)) ||
+      (st = check_cull(out)))
+    return st;
+  if (!ws || !aligned(ws, kAlign)) return NDG_ERR_INVALID_ARG;
+  Sizes z = make_sizes(mix, q, cp, out->E_cap);
+  CommonLayout c = common_layout(z);
+  CullLayout L = cull_layout(z, c.end);
+  if (ws_bytes < L.end) return NDG_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  Tracer tr(trace, s);
+  char* w = (char*)ws;
+  int* status = &reinterpret_cast<WsHeader*>(w + c.header)->status;
+  const int N = mix->N, k = cp->k, KP = z.KP, B = cp->buckets, nb = k > 0 ? B : 1;
+  const long long T = z.T;
+  float* tb = (float*)(w + L.tb);
+  float* range = (float*)(w + L.range);
+  uint8_t* tkey = (uint8_t*)(w + L.tkey);
+  uint8_t* gkey = (uint8_t*)(w + L.gkey);
+  if (k > 0) {
+    tr += launch_tile_bounds(N, q->x, q->Q, q->tile_size, T, k, cp->proj, tb, s);
+    tr += launch_cull_range(tb, T, k, B, q->Q, range, s);
+    tr += launch_tile_keys(tb, T, k, KP, B, range, tkey, s);
+  }
+  PrepArgs pa = prep_args(mix);
+  pa.k = k;
+  pa.KP = KP;
+  pa.B = B;
+  pa.proj = cp->proj;
+  pa.cutoff = cp->cutoff;
+  pa.k_sigma = cp->k_sigma;
+  pa.range = range;
+  pa.gkey = k > 0 ? gkey : nullptr;
+  pa.bin = (uint32_t*)(w + L.bin);
+  pa.status = status;
+  tr += launch_prep(N, pa, s);
+  uint32_t* sk;
+  int32_t* sv;
+  tr += radix_sort_pairs((const uint32_t*)(w + L.bin), nullptr, (uint32_t*)(w + L.bk_a),
+                   (int32_t*)(w + L.bv_a), (uint32_t*)(w + L.bk_b), (int32_t*)(w + L.bv_b), pa.Ge,
+                   nullptr, bits_for((long long)nb * nb + 1), w + L.tmp, s, &sk, &sv);
+  long long* binoff = (long long*)(w + L.binoff);
+  tr += bin_boundaries(sk, pa.Ge, nullptr, nb * nb, binoff, s);
+  CullTileArgs ca{};
+  ca.tkey = tkey;
+  ca.gkey = gkey;
+  ca.binoff = binoff;
+  ca.sorted_ids = sv;
+  ca.B = B;
+  ca.counts = (long long*)(w + L.counts);
+  ca.excl = nullptr;
+  ca.ids = nullptr;
+  ca.E_cap = out->E_cap;
+  tr += launch_cull_tile(KP, ca, T, s);
+  long long* excl = (long long*)(w + L.excl);
+  tr += scan_exclusive_i64(ca.counts, excl, T, w + L.tmp, s);
+  finalize_offsets_kernel<<<(unsigned)ceil_div<long long>(T + 1, 256), 256, 0, s>>>(
+      excl, T, out->E_cap, out->offsets, out->E_dev, status);
+  tr += 1;
+  if (out->E_cap > 0) {
+    ca.excl = excl;
+    ca.ids = out->ids;
+    tr.begin();
+    tr += launch_cull_tile(KP, ca, T, s);
+    tr.end();
+  }
+  return cuda_ok();
+}
+
+ndg_status ndg_forward(const ndg_mixture* mix, const ndg_queries* q, const ndg_cull* cull, int mode,
+                       float* y, void* ws, size_t ws_bytes, ndg_stream stream,
+                       ndg_trace* trace) {
+  ndg_status st;
+  if ((st = check_mix(mix)) || (st = check_queries(q)) || (st = check_cull(cull))) return st;
+  if (mode != NDG_MODE_FP32) return NDG_ERR_INVALID_ARG;
+  if (q->Q > 0 && !y) return NDG_ERR_INVALID_ARG;
+  if (!ws || !aligned(ws, kAlign)) return NDG_ERR_INVALID_ARG;
+  Sizes z = make_sizes(mix, q, nullptr, 0);
+  CommonLayout c = common_layout(z);
+  if (ws_bytes < c.end) return NDG_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  Tracer tr(trace, s);
+  char* w = (char*)ws;
+  PrepArgs pa = prep_args(mix);
+  pa.rec = (float*)(w + c.rec);
+  pa.status = &reinterpret_cast<WsHeader*>(w + c.header)->status;
+  tr += launch_prep(mix->N, pa, s);
+  FwdArgs fa{};
+  fa.x = q->x;
+  fa.Q = q->Q;
+  fa.tile = q->tile_size;
+  fa.offsets = cull->offsets;
+  fa.ids = cull->ids;
+  fa.rec = pa.rec;
+  fa.Ge = pa.Ge;
+  fa.y = y;
+  tr.begin();
+  tr += launch_fwd(mix->N, fa, z.T, s);
+  tr.end();
+  return cuda_ok();
+}
+
+ndg_status ndg_loss_l2(long long Q, const float* y, const float* target, float* dy,
+                       double* loss_dev, void* ws, size_t ws_bytes, ndg_stream stream,
+                       ndg_trace* trace) {
+  if (Q < 0 || !loss_dev || (Q > 0 && (!y || !target || !dy))) return NDG_ERR_INVALID_ARG;
+  if (!ws || !aligned(ws, kAlign)) return NDG_ERR_INVALID_ARG;
+  const size_t off = align_up(sizeof(WsHeader));
+  if (ws_bytes < off + kLossParts * sizeof(double)) return NDG_ERR_WORKSPACE;
+  double* part = (double*)((char*)ws + off);
+  Tracer tr(trace, (cudaStream_t)stream);
+  tr.begin();
+  tr += launch_loss(y, target, dy, 3 * Q, part, loss_dev, (cudaStream_t)stream);
+  tr.end();
+  return cuda_ok();
+}
+
+ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q, const ndg_cull* cull,
+                        const float* dy, ndg_mixture* grad, void* ws, size_t ws_bytes,
+                        ndg_stream stream, ndg_trace* trace) {
+  ndg_status st;
+  if ((st = check_mix(mix)) || (st = check_queries(q)) || (st = check_cull(cull))) return st;
+  if (!grad || grad->N != mix->N || grad->G != mix->G || grad->has_children != mix->has_children ||
+      (st = check_mix(grad)))
+    return st ? st : NDG_ERR_INVALID_ARG;
+  if (q->Q > 0 && !dy) return NDG_ERR_INVALID_ARG;
+  if (cull->E_cap >= (1ll << 31)) return NDG_ERR_INVALID_ARG;
+  if (!ws || !aligned(ws, kAlign)) return NDG_ERR_INVALID_ARG;
+  Sizes z = make_sizes(mix, q, nullptr, cull->E_cap);
+  CommonLayout c = common_layout(z);
+  BwdLayout L = bwd_layout(z, c.end);
+  if (ws_bytes < L.end) return NDG_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  Tracer tr(trace, s);
+  char* w = (char*)ws;
+  const int N = mix->N;
+  PrepArgs pa = prep_args(mix);
+  pa.rec = (float*)(w + c.rec);
+  pa.status = &reinterpret_cast<WsHeader*>(w + c.header)->status;
+  tr += launch_prep(N, pa, s);
+  BwdArgs ba{};
+  ba.x = q->x;
+  ba.dy = dy;
+  ba.Q = q->Q;
+  ba.tile = q->tile_size;
+  ba.offsets = cull->offsets;
+  ba.ids = cull->ids;
+  ba.rec = pa.rec;
+  ba.Ge = pa.Ge;
+  ba.part = (float*)(w + L.part);
+  tr.begin();
+  tr += launch_bwd(N, ba, z.T, s);
+  tr.end();
+  const int Ge = pa.Ge;
+  uint32_t* sk;
+  int32_t* sv;
+  tr += radix_sort_pairs((const uint32_t*)cull->ids, nullptr, (uint32_t*)(w + L.sk_a),
+                   (int32_t*)(w + L.sv_a), (uint32_t*)(w + L.sk_b), (int32_t*)(w + L.sv_b),
+                   cull->E_cap, cull->E_dev, bits_for(Ge > 0 ? Ge : 1), w + L.tmp, s, &sk, &sv);
+  long long* goff = (long long*)(w + L.goff);
+  tr += bin_boundaries(sk, cull->E_cap, cull->E_dev, Ge, goff, s);
+  float* gsum = (float*)(w + L.gsum);
+  tr += launch_segsum(ba.part, part_floats(N), sv, goff, Ge, gsum, s);
+  ChainArgs ch{};
+  ch.G = mix->G;
+  ch.has_children = mix->has_children;
+  ch.gsum = gsum;
+  ch.theta = mix->theta;
+  ch.alpha_raw = mix->alpha_raw;
+  ch.color_raw = mix->color_raw;
+  ch.u_theta = mix->u_theta;
+  ch.m_u = mix->m_u;
+  ch.c_alpha_raw = mix->c_alpha_raw;
+  ch.c_color_raw = mix->c_color_raw;
+  ch.g_mean = grad->mean;
+  ch.g_theta = grad->theta;
+  ch.g_alpha = grad->alpha_raw;
+  ch.g_color = grad->color_raw;
+  ch.g_u_theta = grad->u_theta;
+  ch.g_m_u = grad->m_u;
+  ch.g_c_alpha = grad->c_alpha_raw;
+  ch.g_c_color = grad->c_color_raw;
+  tr += launch_chain(N, ch, s);
+  return cuda_ok();
+}
+
+ndg_status ndg_adam(ndg_mixture* params, const ndg_mixture* grad, ndg_mixture* m1,
+                    ndg_mixture* m2, int* step_dev, float lr, float beta1, float beta2, float eps,
+                    ndg_stream stream, ndg_trace* trace) {
+  ndg_status st;
+  if ((st = check_mix(params)) || (st = check_mix(grad)) || (st = check_mix(m1)) ||
+      (st = check_mix(m2)))
+    return st;
+  if (!step_dev) return NDG_ERR_INVALID_ARG;
+  const ndg_mixture* all[4] = {params, grad, m1, m2};
+  for (const ndg_mixture* m : all)
+    if (m->N != params->N || m->G != params->G || m->has_children != params->has_children)
+      return NDG_ERR_INVALID_ARG;
+  const long long G = params->G, N = params->N, P = tri(params->N);
+  AdamArgs a{};
+  const long long width[8] = {N, P, 1, 3, P, N, 1, 3};
+  float* pp[8] = {params->mean, params->theta, params->alpha_raw, params->color_raw,
+                  params->u_theta, params->m_u, params->c_alpha_raw, params->c_color_raw};
+  const float* gp[8] = {grad->mean, grad->theta, grad->alpha_raw, grad->color_raw,
+                        grad->u_theta, grad->m_u, grad->c_alpha_raw, grad->c_color_raw};
+  float* mp[8] = {m1->mean, m1->theta, m1->alpha_raw, m1->color_raw,
+                  m1->u_theta, m1->m_u, m1->c_alpha_raw, m1->c_color_raw};
+  float* vp[8] = {m2->mean, m2->theta, m2->alpha_raw, m2->color_raw,
+                  m2->u_theta, m2->m_u, m2->c_alpha_raw, m2->c_color_raw};
+  const int nseg = params->has_children ? 8 : 4;
+  for (int i = 0; i < nseg; ++i) a.seg[i] = AdamSeg{pp[i], gp[i], mp[i], vp[i], G * width[i]};
+  a.nseg = G > 0 ? nseg : 0;
+  a.step = step_dev;
+  a.lr = lr;
+  a.b1 = beta1;
+  a.b2 = beta2;
+  a.eps = eps;
+  Tracer tr(trace, (cudaStream_t)stream);
+  tr.begin();
+  tr += launch_adam(a, (cudaStream_t)stream);
+  tr.end();
+  return cuda_ok();
+}
+
+ndg_status ndg_densify(ndg_mixture* mix, float a_thr, float a_child0, const float* noise,
+                       ndg_mixture* m1, ndg_mixture* m2, int* G_new_dev, void* ws,
+                       size_t ws_bytes, ndg_stream stream, ndg_trace* trace) {
+  ndg_status st;
+  if ((st = check_mix(mix))) return st;
+  if (!noise || !G_new_dev || !m1 || !m2) return NDG_ERR_INVALID_ARG;
+  if (!mix->u_theta || !mix->m_u || !mix->c_alpha_raw || !mix->c_color_raw)
+    return NDG_ERR_INVALID_ARG;
+  if (!ws || !aligned(ws, kAlign)) return NDG_ERR_INVALID_ARG;
+  Sizes z = make_sizes(mix, nullptr, nullptr, 0);
+  CommonLayout c = common_layout(z);
+  if (ws_bytes < c.end) return NDG_ERR_WORKSPACE;
+  char* w = (char*)ws;
+  DensifyArgs a{};
+  a.G = mix->G;
+  a.G_cap = mix->G_cap;
+  a.has_children = mix->has_children;
+  a.a_thr = a_thr;
+  a.a_child0 = a_child0;
+  a.mean = mix->mean;
+  a.theta = mix->theta;
+  a.alpha_raw = mix->alpha_raw;
+  a.color_raw = mix->color_raw;
+  a.u_theta = mix->u_theta;
+  a.m_u = mix->m_u;
+  a.c_alpha_raw = mix->c_alpha_raw;
+  a.c_color_raw = mix->c_color_raw;
+  a.noise = noise;
+  const ndg_mixture* moms[2] = {m1, m2};
+  for (int i = 0; i < 2; ++i)
+    a.mom[i] = MomentPtrs{moms[i]->mean, moms[i]->theta, moms[i]->alpha_raw, moms[i]->color_raw,
+                          moms[i]->u_theta, moms[i]->m_u, moms[i]->c_alpha_raw,
+                          moms[i]->c_color_raw};
+  a.flag = (int*)(w + c.dflag);
+  a.rank = (int*)(w + c.drank);
+  a.fresh = (int*)(w + c.dfresh);
+  a.G_new = G_new_dev;
+  Tracer tr(trace, (cudaStream_t)stream);
+  tr.begin();
+  tr += launch_densify(mix->N, a, (cudaStream_t)stream);
+  tr.end();
+  return cuda_ok();
+}
+
+ndg_status ndg_read_status(void* ws, ndg_stream stream, int* device_status) {
+  if (!ws || !device_status) return NDG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return NDG_ERR_CUDA;
+  int v = 0;
+  if (cudaMemcpy(&v, ws, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return NDG_ERR_CUDA;
+  if (cudaMemset(ws, 0, sizeof(int)) != cudaSuccess) return NDG_ERR_CUDA;
+  *device_status = v;
+  return NDG_OK;
+}
+
+const char* ndg_status_string(int status) {
+  switch (status) {
+    case NDG_OK: return "ok";
+    case NDG_ERR_INVALID_ARG: return "invalid argument";
+    case NDG_ERR_CAPACITY: return "candidate capacity exceeded";
+    case NDG_ERR_CUDA: return "CUDA error";
+    case NDG_ERR_NUMERIC: return "non-finite parameter";
+    case NDG_ERR_TIMEOUT: return "device wait timed out";
+    case NDG_ERR_WORKSPACE: return "workspace too small";
+    default: return "unknown status";
+  }
+}
+
+int ndg_version(void) { return 1; }
+
+}  // extern "C"

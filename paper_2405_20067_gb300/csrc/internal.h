@@ -1,0 +1,34 @@
+// internal.h -- host-side launchers shared between the libndg translation
+// units (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace ndg {
+
+// ---- primitives (primitives.cu) ------------------------------------------
+// Exclusive prefix sum of n int64 values: out[0..n], out[n] = total.
+// Every launcher returns the number of kernels it launched.
+size_t scan_temp_bytes(long long n);
+int scan_exclusive_i64(const long long* in, long long* out, long long n, void* temp,
+                        cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs on the low `bits` key bits.
+// The element count is n_cap, or min(*n_dev, n_cap) when n_dev is given
+// (read on the device, so the call can sit in a CUDA graph).  The input
+// (keys_in, vals_in) is only read; vals_in == NULL means values 0, 1, 2, ...
+// Buffers a and b (n_cap elements each) are the ping-pong storage; the
+// result is returned in (keys_out, vals_out), one of the two.
+size_t radix_temp_bytes(long long n_cap);
+int radix_sort_pairs(const uint32_t* keys_in, const int32_t* vals_in, uint32_t* keys_a,
+                      int32_t* vals_a, uint32_t* keys_b, int32_t* vals_b, long long n_cap,
+                      const long long* n_dev, int bits, void* temp, cudaStream_t s,
+                      uint32_t** keys_out, int32_t** vals_out);
+
+// off[b] = first position whose sorted key is >= b, for b in [0, nbins];
+// keys >= nbins count as nbins.
+int bin_boundaries(const uint32_t* sorted, long long n_cap, const long long* n_dev,
+                    int nbins, long long* off, cudaStream_t s);
+
+}  // namespace ndg

@@ -1,0 +1,115 @@
+// kernels.h -- argument blocks and launchers of the libndg kernels
+// (internal; not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ndg {
+
+struct PrepArgs {
+  int G, Ge;
+  const float *mean, *theta, *alpha_raw, *color_raw;
+  const float *u_theta, *m_u, *c_alpha_raw, *c_color_raw;
+  float* rec;  // [Ge][rec_floats(N)] or null
+  // cull keys (when gkey or bin is set)
+  int k, KP, B;
+  const float* proj;
+  float cutoff, k_sigma;
+  const float* range;  // lo, hi, inv_h, NDG_MAX_K each
+  uint8_t* gkey;       // [Ge][2 KP] or null
+  uint32_t* bin;       // [Ge] or null
+  int* status;
+};
+
+struct CullTileArgs {
+  const uint8_t* tkey;        // [T][2 KP]
+  const uint8_t* gkey;        // [Ge][2 KP]
+  const long long* binoff;    // [nb * nb + 1]
+  const int32_t* sorted_ids;  // Gaussians sorted by bin
+  int B;
+  long long* counts;          // count pass: [T]
+  const long long* excl;      // fill pass: exclusive scan of counts
+  int* ids;                   // fill pass: [E_cap]
+  long long E_cap;
+};
+
+struct FwdArgs {
+  const float* x;
+  long long Q;
+  int tile;
+  const long long* offsets;  // [T+1]
+  const int* ids;
+  const float* rec;          // [Ge][rec_floats(N)]
+  int Ge;
+  float* y;                  // [Q][3]
+};
+
+struct BwdArgs {
+  const float* x;
+  const float* dy;
+  long long Q;
+  int tile;
+  const long long* offsets;
+  const int* ids;
+  const float* rec;
+  int Ge;
+  float* part;               // [E_cap][part_floats(N)]
+};
+
+struct ChainArgs {
+  int G, has_children;
+  const float* gsum;         // [Ge][part_floats(N)]
+  const float *theta, *alpha_raw, *color_raw, *u_theta, *m_u, *c_alpha_raw, *c_color_raw;
+  float *g_mean, *g_theta, *g_alpha, *g_color, *g_u_theta, *g_m_u, *g_c_alpha, *g_c_color;
+};
+
+struct AdamSeg {
+  float* p;
+  const float* g;
+  float* m;
+  float* v;
+  long long n;
+};
+
+struct AdamArgs {
+  AdamSeg seg[8];
+  int nseg;
+  int* step;
+  float lr, b1, b2, eps;
+};
+
+struct MomentPtrs {
+  float *mean, *theta, *alpha_raw, *color_raw, *u_theta, *m_u, *c_alpha_raw, *c_color_raw;
+};
+
+struct DensifyArgs {
+  int G, G_cap, has_children;
+  float a_thr, a_child0;
+  float *mean, *theta, *alpha_raw, *color_raw, *u_theta, *m_u, *c_alpha_raw, *c_color_raw;
+  const float* noise;  // [G_cap][P + N + 4]
+  MomentPtrs mom[2];
+  int* flag;           // [G_cap] workspace
+  int* rank;           // [G_cap] workspace
+  int* fresh;          // [G_cap] workspace
+  int* G_new;          // [1] caller
+};
+
+int launch_tile_bounds(int N, const float* x, long long Q, int tile, long long T, int k,
+                        const float* proj, float* tb, cudaStream_t s);
+int launch_cull_range(const float* tb, long long T, int k, int B, long long Q, float* range,
+                       cudaStream_t s);
+int launch_tile_keys(const float* tb, long long T, int k, int KP, int B, const float* range,
+                      uint8_t* tkey, cudaStream_t s);
+int launch_prep(int N, const PrepArgs& a, cudaStream_t s);
+int launch_cull_tile(int KP, const CullTileArgs& a, long long T, cudaStream_t s);
+int launch_fwd(int N, const FwdArgs& a, long long T, cudaStream_t s);
+int launch_loss(const float* y, const float* target, float* dy, long long n, double* part,
+                 double* loss, cudaStream_t s);
+int launch_bwd(int N, const BwdArgs& a, long long T, cudaStream_t s);
+int launch_segsum(const float* part, int RP, const int32_t* gidx, const long long* goff, int Ge,
+                   float* gsum, cudaStream_t s);
+int launch_chain(int N, const ChainArgs& a, cudaStream_t s);
+int launch_adam(const AdamArgs& a, cudaStream_t s);
+int launch_densify(int N, const DensifyArgs& a, cudaStream_t s);
+
+}  // namespace ndg

@@ -1,0 +1,230 @@
+// primitives.cu -- scan, stable radix sort and bin boundaries used by the
+// cull (bucket sort of Gaussians) and by the backward pass (transposing the
+// tile-major candidate lists to Gaussian-major order without atomics).
+#include "common.cuh"
+#include "internal.h"
+
+namespace ndg {
+
+// ---- exclusive scan -------------------------------------------------------
+constexpr int SC_THREADS = 1024;
+constexpr int SC_ITEMS = 4;
+constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
+
+__device__ __forceinline__ long long warp_incl_scan(long long v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    long long u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the total.
+__device__ long long block_excl_scan(long long v, long long* out_excl) {
+  __shared__ long long wsum[32];
+  __shared__ long long wtotal;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  long long incl = warp_incl_scan(v);
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    long long s = lane < nw ? wsum[lane] : 0;
+    long long si = warp_incl_scan(s);
+    if (lane < nw) wsum[lane] = si - s;
+    if (lane == 31) wtotal = si;  // nw <= 32
+  }
+  __syncthreads();
+  *out_excl = incl - v + wsum[warp];
+  long long total = wtotal;
+  __syncthreads();
+  return total;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) scan_tiles(const long long* in, long long* out,
+                                                         long long n, long long* bsum) {
+  long long base = (long long)blockIdx.x * SC_TILE + (long long)threadIdx.x * SC_ITEMS;
+  long long v[SC_ITEMS], s = 0;
+#pragma unroll
+  for (int i = 0; i < SC_ITEMS; ++i) {
+    v[i] = base + i < n ? in[base + i] : 0;
+    s += v[i];
+  }
+  long long ex;
+  long long total = block_excl_scan(s, &ex);
+#pragma unroll
+  for (int i = 0; i < SC_ITEMS; ++i) {
+    if (base + i < n) out[base + i] = ex;
+    ex += v[i];
+  }
+  if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+// One block scans the block sums in place (exclusive) and writes the total.
+__global__ void __launch_bounds__(SC_THREADS) scan_sums(long long* bsum, long long nb,
+                                                        long long* total_out) {
+  long long carry = 0;
+  for (long long c = 0; c < nb; c += SC_THREADS) {
+    long long i = c + threadIdx.x;
+    long long v = i < nb ? bsum[i] : 0, ex;
+    long long t = block_excl_scan(v, &ex);
+    if (i < nb) bsum[i] = ex + carry;
+    carry += t;
+  }
+  if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) scan_add(long long* out, long long n,
+                                                       const long long* bsum) {
+  long long base = (long long)blockIdx.x * SC_TILE + (long long)threadIdx.x * SC_ITEMS;
+  long long add = bsum[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < SC_ITEMS; ++i)
+    if (base + i < n) out[base + i] += add;
+}
+
+size_t scan_temp_bytes(long long n) {
+  long long nb = ceil_div<long long>(n > 0 ? n : 1, SC_TILE);
+  return (size_t)(nb + 1) * sizeof(long long);
+}
+
+int scan_exclusive_i64(const long long* in, long long* out, long long n, void* temp,
+                       cudaStream_t s) {
+  long long nb = ceil_div<long long>(n > 0 ? n : 1, SC_TILE);
+  long long* bsum = (long long*)temp;
+  scan_tiles<<<(unsigned)nb, SC_THREADS, 0, s>>>(in, out, n, bsum);
+  scan_sums<<<1, SC_THREADS, 0, s>>>(bsum, nb, out + n);
+  if (nb > 1) {
+    scan_add<<<(unsigned)nb, SC_THREADS, 0, s>>>(out, n, bsum);
+    return 3;
+  }
+  return 2;
+}
+
+// ---- stable LSD radix sort, 8 bits per pass -------------------------------
+constexpr int RS_THREADS = 256;
+constexpr int RS_ROUNDS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
+
+__device__ __forceinline__ long long rs_count(long long n_cap, const long long* n_dev) {
+  if (!n_dev) return n_cap;
+  long long n = *n_dev;
+  return n < n_cap ? (n < 0 ? 0 : n) : n_cap;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) rs_hist(const uint32_t* keys, long long n_cap,
+                                                      const long long* n_dev, int shift,
+                                                      long long* counts, int nblocks) {
+  __shared__ int h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const long long n = rs_count(n_cap, n_dev);
+  const long long base = (long long)blockIdx.x * RS_TILE;
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    long long i = base + r * RS_THREADS + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1);
+  }
+  __syncthreads();
+  counts[(long long)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// Scatter with ranks that keep the input order among equal digits: elements
+// are taken in rounds of 256 in index order; inside a round the rank of an
+// element is (earlier rounds) + (lower warps of this round) + (lower lanes).
+__global__ void __launch_bounds__(RS_THREADS) rs_scatter(const uint32_t* kin, const int32_t* vin,
+                                                         uint32_t* kout, int32_t* vout,
+                                                         long long n_cap, const long long* n_dev,
+                                                         int shift, const long long* offs,
+                                                         int nblocks) {
+  constexpr int NW = RS_THREADS / 32;
+  __shared__ long long run[256];
+  __shared__ int wc[NW][256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  run[tid] = offs[(long long)tid * nblocks + blockIdx.x];
+  const long long n = rs_count(n_cap, n_dev);
+  const long long base = (long long)blockIdx.x * RS_TILE;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) wc[w][tid] = 0;
+    __syncthreads();
+    long long i = base + r * RS_THREADS + tid;
+    bool valid = i < n;
+    uint32_t key = valid ? kin[i] : 0u;
+    int d = valid ? (int)((key >> shift) & 255u) : 256 + lane;  // invalid lanes match nobody
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    int wrank = __popc(peers & lt_mask);
+    if (valid && wrank == 0) wc[warp][d] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      long long pos = run[d] + wrank;
+      for (int w = 0; w < warp; ++w) pos += wc[w][d];
+      kout[pos] = key;
+      vout[pos] = vin ? vin[i] : (int32_t)i;
+    }
+    __syncthreads();
+    int add = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) add += wc[w][tid];
+    run[tid] += add;
+    __syncthreads();
+  }
+}
+
+size_t radix_temp_bytes(long long n_cap) {
+  long long nb = ceil_div<long long>(n_cap > 0 ? n_cap : 1, RS_TILE);
+  size_t counts = (size_t)(256 * nb + 1) * sizeof(long long);
+  counts = (counts + 255) / 256 * 256;
+  return 2 * counts + scan_temp_bytes(256 * nb);
+}
+
+int radix_sort_pairs(const uint32_t* keys_in, const int32_t* vals_in, uint32_t* keys_a,
+                      int32_t* vals_a, uint32_t* keys_b, int32_t* vals_b, long long n_cap,
+                      const long long* n_dev, int bits, void* temp, cudaStream_t s,
+                      uint32_t** keys_out, int32_t** vals_out) {
+  long long nb = ceil_div<long long>(n_cap > 0 ? n_cap : 1, RS_TILE);
+  size_t counts_b = ((size_t)(256 * nb + 1) * sizeof(long long) + 255) / 256 * 256;
+  long long* counts = (long long*)temp;
+  long long* offs = (long long*)((char*)temp + counts_b);
+  void* stemp = (char*)temp + 2 * counts_b;
+  const int passes = bits < 1 ? 1 : (bits + 7) / 8;
+  uint32_t* kbuf[2] = {keys_a, keys_b};
+  int32_t* vbuf[2] = {vals_a, vals_b};
+  int launched = 0;
+  for (int p = 0; p < passes; ++p) {
+    // pass p reads buffer p & 1 (the caller's input on pass 0) and writes the other
+    const uint32_t* ksrc = p == 0 ? keys_in : kbuf[p & 1];
+    const int32_t* vsrc = p == 0 ? vals_in : vbuf[p & 1];
+    const int dst = (p + 1) & 1;
+    rs_hist<<<(unsigned)nb, RS_THREADS, 0, s>>>(ksrc, n_cap, n_dev, 8 * p, counts, (int)nb);
+    launched += 2 + scan_exclusive_i64(counts, offs, 256 * nb, stemp, s);
+    rs_scatter<<<(unsigned)nb, RS_THREADS, 0, s>>>(ksrc, vsrc, kbuf[dst], vbuf[dst], n_cap, n_dev,
+                                                   8 * p, offs, (int)nb);
+  }
+  *keys_out = kbuf[passes & 1];
+  *vals_out = vbuf[passes & 1];
+  return launched;
+}
+
+// ---- boundaries of sorted bins --------------------------------------------
+__global__ void bin_bounds_kernel(const uint32_t* sorted, long long n_cap, const long long* n_dev,
+                                  int nbins, long long* off) {
+  const long long n = rs_count(n_cap, n_dev);
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  long long prev = i == 0 ? -1 : (long long)min((uint32_t)nbins, sorted[i - 1]);
+  long long cur = i == n ? nbins : (long long)min((uint32_t)nbins, sorted[i]);
+  for (long long b = prev + 1; b <= cur; ++b) off[b] = i;
+}
+
+int bin_boundaries(const uint32_t* sorted, long long n_cap, const long long* n_dev, int nbins,
+                   long long* off, cudaStream_t s) {
+  long long threads = n_cap + 1;
+  bin_bounds_kernel<<<(unsigned)ceil_div<long long>(threads, 256), 256, 0, s>>>(sorted, n_cap, n_dev,
+                                                                             nbins, off);
+  return 1;
+}
+
+}  // namespace ndg

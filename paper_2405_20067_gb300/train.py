@@ -1,0 +1,171 @@
+"""Differentiable evaluation and the fit loop (Sections 3.3 and 4.1).
+
+NDGEval is a torch.autograd.Function whose forward is ndg_forward and whose
+backward is ndg_backward; Trainer drives the fit: per step the cull
+(ndg_build_cull), the evaluation, the plain L2 loss (ndg_loss_l2), the
+analytic backward, Adam (ndg_adam) and, at phase boundaries, the refinement
+(ndg_densify).  Every step of that path runs in libndg's kernels; torch
+provides device memory, streams and the autograd plumbing only.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import ndg
+
+_PARAMS = ["mean", "theta", "alpha_raw", "color_raw", "u_theta", "m_u", "c_alpha_raw",
+           "c_color_raw"]
+
+
+class NDGEval(torch.autograd.Function):
+    """y = culled mixture value at the evaluator's queries (Eq. 1, Eq. 8).
+    Gradients flow to the eight raw parameter tensors of the mixture."""
+
+    @staticmethod
+    def forward(ctx, ev: ndg.Evaluator, mix: ndg.Mixture, *params):
+        y = torch.empty(ev.x.shape[0], 3, dtype=torch.float32, device=ev.x.device)
+        ndg.forward(mix, ev.x, ev.tile, ev.cull, y, ev.ws, trace=getattr(ev, "trace_fwd", None))
+        ctx.ev, ctx.mix = ev, mix
+        return y
+
+    @staticmethod
+    def backward(ctx, dy):
+        ev, mix = ctx.ev, ctx.mix
+        # fresh (uninitialised) gradient tensors: autograd adopts them as
+        # .grad without a copy; rows >= G are never read
+        grad = ndg.Mixture(mix.N, mix.G, *[None if getattr(mix, f) is None
+                                           else torch.empty_like(getattr(mix, f))
+                                           for f in _PARAMS], has_children=mix.has_children)
+        ndg.backward(mix, ev.x, ev.tile, ev.cull, dy.contiguous(), grad, ev.ws,
+                     trace=getattr(ev, "trace_bwd", None))
+        outs = [getattr(grad, f) if (mix.has_children or i < 4) else None
+                for i, f in enumerate(_PARAMS)]
+        return (None, None, *outs)
+
+
+def evaluate(ev: ndg.Evaluator, mix: ndg.Mixture) -> torch.Tensor:
+    """Differentiable evaluation; mix tensors must require grad for a backward."""
+    return NDGEval.apply(ev, mix, *[getattr(mix, f) for f in _PARAMS])
+
+
+class Trainer:
+    """Adam fit of a mixture to targets at a fixed query set.
+
+    step() does one whole iteration on the device without host
+    synchronisation; the candidate capacity is checked by check()."""
+
+    def __init__(self, mix: ndg.Mixture, x: torch.Tensor, target: torch.Tensor, tile: int,
+                 cp: ndg.CullParams, lr: float = 1e-3, t: float = 0.01, phase: int = 300,
+                 E_cap: int | None = None, seed: int = 0):
+        self.mix, self.tile, self.cp = mix, tile, cp
+        self.lr, self.t, self.phase = lr, t, phase
+        for f in _PARAMS:
+            p = getattr(mix, f)
+            if p is not None:
+                p.requires_grad_(True)
+        self.m1, self.m2 = mix.zeros_like(), mix.zeros_like()
+        for m in (self.m1, self.m2):
+            for f in _PARAMS:
+                if getattr(m, f) is not None:
+                    getattr(m, f).requires_grad_(False)
+        self.x = x.contiguous()
+        self.target = target.contiguous()
+        self.ev = ndg.Evaluator(mix, self.x, tile, cp, E_cap=E_cap)
+        if E_cap is None:  # size the candidate buffers once from the initial state
+            E = self.ev.build(mix)
+            self.ev = ndg.Evaluator(mix, self.x, tile, cp, E_cap=int(E * 1.5) + 4096)
+        dev = self.x.device
+        self.dy = torch.empty_like(self.target)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.step_dev = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.G_new = torch.zeros(1, dtype=torch.int32, device=dev)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(seed)
+        P = mix.N * (mix.N + 1) // 2
+        self.noise = torch.randn(mix.G_cap, P + mix.N + 4, device=dev, generator=gen)
+        self.iteration = 0
+        self.traces = None
+
+    def set_traces(self, traces: dict | None):
+        """traces: dict name -> ndg.Trace for build_cull / forward / loss /
+        backward / adam / densify, or None."""
+        self.traces = traces
+        self.ev.trace_fwd = traces.get("forward") if traces else None
+        self.ev.trace_bwd = traces.get("backward") if traces else None
+
+    def _tr(self, name):
+        return self.traces.get(name) if self.traces else None
+
+    def step(self, x: torch.Tensor | None = None, target: torch.Tensor | None = None,
+             refine: bool | None = None) -> torch.Tensor:
+        """One iteration; x / target (host or device) replace the query set's
+        contents when given.  Returns the loss as a device tensor."""
+        if x is not None:
+            self.x.copy_(x, non_blocking=True)
+        if target is not None:
+            self.target.copy_(target, non_blocking=True)
+        mix = self.mix
+        ndg.build_cull(mix, self.x, self.tile, self.cp, self.ev.cull, self.ev.ws,
+                       trace=self._tr("build_cull"))
+        with torch.enable_grad():
+            y = evaluate(self.ev, mix)
+            ndg.loss_l2(y.detach(), self.target, self.dy, self.loss, self.ev.ws,
+                        trace=self._tr("loss"))
+            y.backward(self.dy)
+        grad = ndg.Mixture(mix.N, mix.G, *[getattr(mix, f).grad if getattr(mix, f) is not None
+                                           else None for f in _PARAMS],
+                           has_children=mix.has_children)
+        if not mix.has_children:
+            grad.u_theta = grad.m_u = grad.c_alpha_raw = grad.c_color_raw = None
+        with torch.no_grad():
+            pm = self._detached(mix)
+            ndg.adam(pm, grad, self._sync_meta(self.m1), self._sync_meta(self.m2), self.step_dev,
+                     self.lr, trace=self._tr("adam"))
+        for f in _PARAMS:
+            if getattr(mix, f) is not None:
+                getattr(mix, f).grad = None
+        self.iteration += 1
+        if refine is None:
+            refine = self.phase > 0 and self.iteration % self.phase == 0
+        if refine:
+            self.refine(sync=False)
+        return self.loss
+
+    def _detached(self, mix):
+        return ndg.Mixture(mix.N, mix.G, *[None if getattr(mix, f) is None
+                                           else getattr(mix, f).detach() for f in _PARAMS],
+                           has_children=mix.has_children)
+
+    def _sync_meta(self, m):
+        m.G, m.has_children = self.mix.G, self.mix.has_children
+        return m
+
+    def refine(self, sync: bool = True):
+        """Section 3.3 refinement.  With sync the new row count is read back
+        and the mixture grows; without it the count stays on the device and
+        check() applies it."""
+        pm = self._detached(self.mix)
+        ndg.densify_async(pm, self.t, self.noise, self._sync_meta(self.m1),
+                          self._sync_meta(self.m2), self.G_new, self.ev.ws,
+                          trace=self._tr("densify"))
+        self.mix.has_children = True
+        if sync:
+            self.check()
+
+    def check(self):
+        """Synchronises: applies a pending row count, verifies the device
+        status word and the candidate capacity (rebuilding larger buffers
+        when it overflowed)."""
+        st = ndg.read_status(self.ev.ws)
+        Gn = int(self.G_new.item())
+        if self.mix.has_children and Gn >= self.mix.G:
+            self.mix.G = Gn
+        self._sync_meta(self.m1)
+        self._sync_meta(self.m2)
+        if st == ndg.NDG_ERR_CAPACITY or self.ev.cull.E() > self.ev.E_cap:
+            E = self.ev.cull.E()
+            self.ev = ndg.Evaluator(self.mix, self.x, self.tile, self.cp, E_cap=int(E * 1.5) + 4096)
+            self.set_traces(self.traces)
+        elif st != ndg.NDG_OK:
+            raise ndg.NDGError(st, "device status")
+        return st

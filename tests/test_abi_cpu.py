@@ -1,0 +1,90 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every symbol include/ndg.h declares, sizes workspaces, and rejects bad
+arguments before launching anything."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ndg():
+    from paper_2405_20067_gb300 import build, ndg
+    build.build()
+    return ndg
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ndg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ndg_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(ndg):
+    names = declared_functions()
+    assert len(names) >= 10
+    L = ndg.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(names) == sorted(ndg.EXPORTS)
+
+
+def test_version_and_status_strings(ndg):
+    assert ndg.lib().ndg_version() == 1
+    assert ndg.status_string(0) == "ok"
+    assert "capacity" in ndg.status_string(2)
+
+
+def _mix_c(ndg, N=6, G=10, G_cap=10):
+    fake = ctypes.c_void_p(0x1000)
+    return ndg.MixtureC(N, G, G_cap, 0, fake, fake, fake, fake, None, None, None, None)
+
+
+def test_workspace_size_grows_with_capacity(ndg):
+    L = ndg.lib()
+    m = _mix_c(ndg)
+    q = ndg.QueriesC(1000, 256, ctypes.c_void_p(0x2000))
+    cp = ndg.CullParamsC(16, ctypes.c_void_p(0x3000), 1.0 / 255, 3.0, 64)
+    a = L.ndg_workspace_size(ctypes.byref(m), ctypes.byref(q), ctypes.byref(cp), 0)
+    b = L.ndg_workspace_size(ctypes.byref(m), ctypes.byref(q), ctypes.byref(cp), 10_000)
+    assert 0 < a < b
+    bad = _mix_c(ndg, N=13)
+    assert L.ndg_workspace_size(ctypes.byref(bad), None, None, 0) == 0
+
+
+def test_invalid_arguments_rejected_on_host(ndg):
+    """Each case fails argument validation before any CUDA call."""
+    L = ndg.lib()
+    ws = ctypes.c_void_p(0x100000)
+    q = ndg.QueriesC(100, 256, ctypes.c_void_p(0x2000))
+    cp = ndg.CullParamsC(4, ctypes.c_void_p(0x3000), 0.0, 3.0, 64)
+    cull = ndg.CullC(ctypes.c_void_p(0x4000), ctypes.c_void_p(0x5000), 100, ctypes.c_void_p(0x6000))
+    BIG = 1 << 40
+    cases = [
+        (_mix_c(ndg, N=0), q, cp),                       # N out of range
+        (_mix_c(ndg, N=13), q, cp),                      # N out of range
+        (_mix_c(ndg, G=11, G_cap=10), q, cp),            # G > G_cap
+        (_mix_c(ndg), ndg.QueriesC(100, 0, ctypes.c_void_p(0x2000)), cp),    # tile 0
+        (_mix_c(ndg), ndg.QueriesC(100, 257, ctypes.c_void_p(0x2000)), cp),  # tile > 256
+        (_mix_c(ndg), ndg.QueriesC(100, 256, None), cp),                      # x NULL
+        (_mix_c(ndg), q, ndg.CullParamsC(33, ctypes.c_void_p(0x3000), 0.0, 3.0, 64)),  # k > 32
+        (_mix_c(ndg), q, ndg.CullParamsC(4, None, 0.0, 3.0, 64)),                      # proj NULL
+        (_mix_c(ndg), q, ndg.CullParamsC(4, ctypes.c_void_p(0x3000), 0.0, 3.0, 256)),  # B > 255
+        (_mix_c(ndg), q, ndg.CullParamsC(4, ctypes.c_void_p(0x3000), -1.0, 3.0, 64)),  # cutoff < 0
+    ]
+    for m, qq, cc in cases:
+        st = L.ndg_build_cull(ctypes.byref(m), ctypes.byref(qq), ctypes.byref(cc),
+                              ctypes.byref(cull), ws, BIG, None, None)
+        assert st == 1, (m.N, m.G, qq.tile_size, cc.k)
+    # misaligned workspace and a workspace that is too small
+    m = _mix_c(ndg)
+    assert L.ndg_build_cull(ctypes.byref(m), ctypes.byref(q), ctypes.byref(cp), ctypes.byref(cull),
+                            ctypes.c_void_p(0x100010), BIG, None, None) == 1
+    assert L.ndg_build_cull(ctypes.byref(m), ctypes.byref(q), ctypes.byref(cp), ctypes.byref(cull),
+                            ws, 1024, None, None) == 6
+    assert L.ndg_forward(ctypes.byref(m), ctypes.byref(q), ctypes.byref(cull), 7,
+                         ctypes.c_void_p(0x7000), ws, BIG, None, None) == 1  # unknown mode
+    assert L.ndg_loss_l2(-1, None, None, None, None, ws, BIG, None, None) == 1

@@ -1,0 +1,272 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the
+same seeded inputs: candidate lists bit-exact, outputs within 1e-5 relative,
+gradients within 1e-4 (tolerances in helpers.py)."""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import (NAMES, assert_grads_close, assert_outputs_close, csr_sets, oracle_raw)
+from paper_2405_20067_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ndg():
+    import torch
+    from paper_2405_20067_gb300 import build, ndg as _ndg
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a GPU"
+    return _ndg
+
+
+def make_case(N, G, Q, seed, children=False, queries="box"):
+    mix = synth.mixture(N, G, seed)
+    ch = synth.children(N, G, seed + 1, spread=0.2) if children else None
+    if queries == "box":
+        x = synth.queries_box(N, Q, seed + 2)
+    else:
+        x = queries
+    return mix, ch, x
+
+
+def gpu_setup(ndg, N, mix, ch, x, tile, k, cutoff, k_sigma, B, seed, E_cap=None, G_cap=None):
+    import torch
+    gm = ndg.Mixture.from_arrays(N, mix, ch, G_cap=G_cap)
+    xt = torch.as_tensor(x).cuda()
+    proj = synth.projections(N, k, seed + 3) if k > 0 else np.zeros((0, N), np.float32)
+    cp = ndg.CullParams(k, torch.as_tensor(proj).cuda() if k > 0 else None, cutoff, k_sigma, B)
+    ev = ndg.Evaluator(gm, xt, tile, cp, E_cap=E_cap)
+    E = ev.build(gm)
+    return gm, xt, proj, cp, ev, E
+
+
+CULL_CASES = [
+    # N, G, Q, tile, k, cutoff, k_sigma, B, children
+    (6, 2000, 20000, 256, 16, 1 / 255, 3.0, 64, False),
+    (6, 1500, 9000, 100, 8, 0.0, 3.0, 200, True),
+    (10, 1200, 12288, 256, 16, 1 / 255, 3.0, 128, False),
+    (3, 500, 5000, 64, 1, 0.0, 2.0, 32, False),
+    (2, 300, 3000, 17, 32, 1 / 255, 3.0, 255, True),
+    (6, 800, 4096, 256, 4, 0.0, 3.0, 1, False),
+    (12, 400, 2000, 256, 24, 1 / 255, 3.0, 16, False),
+]
+
+
+@pytest.mark.parametrize("N,G,Q,tile,k,cutoff,k_sigma,B,children", CULL_CASES)
+def test_cull_lists_bit_exact_and_forward(ndg, oracle, N, G, Q, tile, k, cutoff, k_sigma, B,
+                                          children):
+    seed = 100 + N + k
+    mix, ch, x = make_case(N, G, Q, seed, children)
+    gm, xt, proj, cp, ev, E = gpu_setup(ndg, N, mix, ch, x, tile, k, cutoff, k_sigma, B, seed)
+    raw = oracle_raw(oracle, mix, ch)
+    L, m, w = oracle.activate(raw)
+    offs, ids = oracle.cull_contract(L, m, w, x.astype(np.float64), tile, proj, cutoff, k_sigma, B)
+    assert E == offs[-1], (E, offs[-1])
+    g_off = ev.cull.offsets.cpu().numpy()
+    g_ids = ev.cull.ids[:E].cpu().numpy()
+    assert np.array_equal(g_off, offs)
+    for t, (a, b) in enumerate(zip(csr_sets(g_off, g_ids), csr_sets(offs, ids))):
+        assert np.array_equal(a, b), f"tile {t}: {len(a)} vs {len(b)} candidates"
+    assert 0 < E
+    if k > 0 and B > 1:
+        assert E < len(offs[:-1]) * L.shape[0], "nothing culled"
+    y = ev.forward(gm).cpu().numpy()
+    yo = oracle.eval(L, m, w, x.astype(np.float64), tile, offs, ids)
+    assert_outputs_close(y, yo)
+    assert ndg.read_status(ev.ws) == 0
+
+
+def test_dense_forward_config0(ndg, oracle):
+    """N = 6, 1000 Gaussians, 16384 queries, no culling (k = 0)."""
+    c = synth.config0()
+    N = c["N"]
+    gm, xt, proj, cp, ev, E = gpu_setup(ndg, N, c["mix"], None, c["x"], 256, 0, 0.0, 3.0, 1, 0)
+    assert E == 64 * 1000
+    y = ev.forward(gm).cpu().numpy()
+    raw = oracle_raw(oracle, c["mix"])
+    L, m, w = oracle.activate(raw)
+    yo = oracle.eval(L, m, w, c["x"].astype(np.float64))
+    assert_outputs_close(y, yo)
+
+
+GRAD_CASES = [
+    # N, G, Q, tile, k, cutoff, children
+    (6, 1000, 16384, 256, 0, 0.0, False),
+    (6, 600, 8192, 256, 16, 1 / 255, True),
+    (10, 400, 6000, 128, 16, 1 / 255, True),
+    (3, 200, 3000, 33, 8, 0.0, True),
+]
+
+
+@pytest.mark.parametrize("N,G,Q,tile,k,cutoff,children", GRAD_CASES)
+def test_backward_matches_oracle(ndg, oracle, N, G, Q, tile, k, cutoff, children):
+    import torch
+    seed = 300 + N + k
+    mix, ch, x = make_case(N, G, Q, seed, children)
+    gm, xt, proj, cp, ev, E = gpu_setup(ndg, N, mix, ch, x, tile, k, cutoff, 3.0, 64, seed)
+    dy = (synth.rng(seed + 9).standard_normal((Q, 3)) / (3 * Q)).astype(np.float32)
+    grad = ev.backward(gm, torch.as_tensor(dy).cuda())
+    raw = oracle_raw(oracle, mix, ch)
+    offs = ev.cull.offsets.cpu().numpy()
+    ids_sorted = np.concatenate(csr_sets(offs, ev.cull.ids[:E].cpu().numpy())).astype(np.int32)
+    # the oracle's own lists, identical as sets (checked above)
+    L, m, w = oracle.activate(raw)
+    o_offs, o_ids = (oracle.cull_contract(L, m, w, x.astype(np.float64), tile, proj, cutoff, 3.0, 64)
+                     if k > 0 else (None, None))
+    if k > 0:
+        assert np.array_equal(o_ids, ids_sorted)
+    want = oracle.grad(raw, x.astype(np.float64), tile, o_offs, o_ids, dy.astype(np.float64))
+    names = NAMES if children else NAMES[:4]
+    got = {n: getattr(grad, n)[:G].cpu().numpy() for n in names}
+    assert_grads_close(got, want, names)
+    # determinism: a second backward is bit-identical
+    grad2 = ev.backward(gm, torch.as_tensor(dy).cuda())
+    for n in names:
+        assert torch.equal(getattr(grad, n), getattr(grad2, n)), n
+
+
+def test_loss_matches_oracle(ndg, oracle):
+    import torch
+    r = synth.rng(5)
+    Q = 70001
+    y = r.uniform(0, 2, (Q, 3)).astype(np.float32)
+    t = r.uniform(0, 2, (Q, 3)).astype(np.float32)
+    yt, tt = torch.as_tensor(y).cuda(), torch.as_tensor(t).cuda()
+    dy = torch.empty_like(yt)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ws = ndg.workspace(1 << 16)
+    ndg.loss_l2(yt, tt, dy, loss, ws)
+    lo, go = oracle.loss_l2(y.astype(np.float64), t.astype(np.float64))
+    assert abs(loss.item() - lo) <= 1e-12 * lo
+    assert_outputs_close(dy.cpu().numpy(), go, rtol=1e-6, floor=1e-12)
+
+
+def test_adam_matches_oracle(ndg, oracle):
+    import torch
+    N, G = 6, 500
+    mix = synth.mixture(N, G, 7)
+    ch = synth.children(N, G, 8)
+    p = ndg.Mixture.from_arrays(N, mix, ch, G_cap=G + 10)
+    r = synth.rng(9)
+    grads = {n: r.standard_normal(getattr(p, n).shape).astype(np.float32) for n in NAMES}
+    g = p.zeros_like()
+    for n in NAMES:
+        getattr(g, n).copy_(torch.as_tensor(grads[n]))
+    m1, m2 = p.zeros_like(), p.zeros_like()
+    step = torch.zeros(1, dtype=torch.int32, device="cuda")
+    before = {n: getattr(p, n).cpu().numpy().astype(np.float64) for n in NAMES}
+    for it in range(3):
+        ndg.adam(p, g, m1, m2, step, 1e-2)
+    assert step.item() == 3
+    for n in NAMES:
+        pw = before[n][:G].ravel()
+        om1 = np.zeros_like(pw)
+        om2 = np.zeros_like(pw)
+        for it in range(3):
+            pw, om1, om2 = oracle.adam(pw, grads[n][:G].ravel().astype(np.float64), om1, om2,
+                                       it + 1, 1e-2)
+        got = getattr(p, n)[:G].cpu().numpy().ravel()
+        np.testing.assert_allclose(got, pw, rtol=1e-5, atol=1e-6, err_msg=n)
+        # rows beyond G untouched
+        assert np.array_equal(getattr(p, n)[G:].cpu().numpy(), before[n][G:].astype(np.float32))
+
+
+@pytest.mark.parametrize("first", [True, False])
+def test_densify_matches_oracle(ndg, oracle, first):
+    import torch
+    N, G, cap = 6, 300, 340
+    mix = synth.mixture(N, G, 21)
+    ch = None if first else synth.children(N, G, 22, spread=0.1, brightness=(0.001, 0.03))
+    gm = ndg.Mixture.from_arrays(N, mix, ch, G_cap=cap)
+    m1, m2 = gm.zeros_like(), gm.zeros_like()
+    for mm in (m1, m2):
+        for n in NAMES:
+            getattr(mm, n).fill_(7.0)
+    noise = synth.noise(cap, N, 23)
+    ws = ndg.workspace(ndg.workspace_size(gm, None, 1, None, 0))
+    G_new = torch.zeros(1, dtype=torch.int32, device="cuda")
+    t = 0.01
+    ndg.densify(gm, t, torch.as_tensor(noise).cuda(), m1, m2, G_new, ws)
+    raw = oracle_raw(oracle, mix, ch)
+    a_thr = float(np.float32(math.log(t)))
+    new, Gn, flag = oracle.densify(raw, cap, a_thr, math.log(t / 10), noise.astype(np.float64))
+    assert gm.G == Gn
+    if first:
+        assert Gn == G
+    else:
+        assert Gn == cap, "capacity-limited case expected"
+    for n in NAMES:
+        got = getattr(gm, n)[:Gn].cpu().numpy().astype(np.float64)
+        want = getattr(new, n)[:Gn]
+        np.testing.assert_allclose(got, want, rtol=2e-6, atol=2e-6, err_msg=n)
+    # moments of touched rows zeroed, others kept
+    fresh = np.zeros(cap, bool)
+    fresh[:Gn] = True if first else False
+    if not first:
+        fresh[np.nonzero(flag)[0]] = True
+        fresh[G:Gn] = True
+    c1 = m1.u_theta.cpu().numpy()
+    assert np.all(c1[fresh] == 0) and np.all(c1[~fresh] == 7.0)
+    p1 = m1.mean.cpu().numpy()
+    assert np.all(p1[G:Gn] == 0) and np.all(p1[:G] == 7.0)
+
+
+def test_capacity_overflow_reports_and_truncates(ndg, oracle):
+    import torch
+    N, G, Q, tile = 6, 500, 4096, 256
+    mix, ch, x = make_case(N, G, Q, 41)
+    gm = ndg.Mixture.from_arrays(N, mix)
+    xt = torch.as_tensor(x).cuda()
+    proj = torch.as_tensor(synth.projections(N, 8, 42)).cuda()
+    cp = ndg.CullParams(8, proj, 1 / 255, 3.0, 64)
+    cull = ndg.Cull(16, 100)
+    ws = ndg.workspace(ndg.workspace_size(gm, xt, tile, cp, 100))
+    ndg.build_cull(gm, xt, tile, cp, cull, ws)
+    E = cull.E()
+    assert E > 100
+    assert ndg.read_status(ws) == ndg.NDG_ERR_CAPACITY
+    assert ndg.read_status(ws) == 0  # reading clears
+    offs = cull.offsets.cpu().numpy()
+    assert offs.max() <= 100 and np.all(np.diff(offs) >= 0)
+
+
+def test_empty_inputs(ndg):
+    import torch
+    N = 6
+    mix = synth.mixture(N, 10, 3)
+    gm = ndg.Mixture.from_arrays(N, mix)
+    proj = torch.as_tensor(synth.projections(N, 4, 1)).cuda()
+    cp = ndg.CullParams(4, proj, 1 / 255, 3.0, 64)
+    # no queries
+    x0 = torch.zeros(0, N, device="cuda")
+    ev = ndg.Evaluator(gm, x0, 256, cp, E_cap=16)
+    assert ev.build(gm) == 0
+    assert ev.forward(gm).shape == (0, 3)
+    # no Gaussians
+    g0 = ndg.Mixture.from_arrays(N, {k: v[:0] for k, v in mix.items()}, G_cap=4)
+    x = torch.as_tensor(synth.queries_box(N, 300, 2)).cuda()
+    ev = ndg.Evaluator(g0, x, 256, cp, E_cap=16)
+    assert ev.build(g0) == 0
+    y = ev.forward(g0)
+    assert torch.count_nonzero(y) == 0
+    grad = ev.backward(g0, torch.ones(300, 3, device="cuda"))
+    assert ndg.read_status(ev.ws) == 0
+
+
+def test_value_at_mean_exact(ndg):
+    """Eq. 1: a query at a Gaussian's mean with nothing else nearby returns w
+    to FP32 rounding (s = 0 exactly, exp2(0) = 1)."""
+    import torch
+    N = 6
+    mix = synth.mixture(N, 1, 4)
+    gm = ndg.Mixture.from_arrays(N, mix)
+    x = torch.as_tensor(mix["mean"]).cuda()
+    cp = ndg.CullParams(0, None, 0.0, 3.0, 1)
+    ev = ndg.Evaluator(gm, x, 1, cp, E_cap=4)
+    ev.build(gm)
+    y = ev.forward(gm).cpu().numpy()[0]
+    a = np.float64(mix["alpha_raw"][0])
+    c = 1.0 / (1.0 + np.exp(-mix["color_raw"][0].astype(np.float64)))
+    np.testing.assert_allclose(y, np.exp(a) * c, rtol=1e-6)

@@ -1,0 +1,70 @@
+"""The autograd Function and the fit loop on the GPU."""
+import numpy as np
+import pytest
+
+from paper_2405_20067_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ndg():
+    import torch
+    from paper_2405_20067_gb300 import build, ndg as _ndg
+    build.build()
+    assert torch.cuda.is_available()
+    return _ndg
+
+
+def test_autograd_function_matches_direct_backward(ndg):
+    import torch
+    from paper_2405_20067_gb300.train import evaluate
+    N, G, Q = 6, 500, 4096
+    mix = synth.mixture(N, G, 1)
+    ch = synth.children(N, G, 2, spread=0.2)
+    gm = ndg.Mixture.from_arrays(N, mix, ch)
+    x = torch.as_tensor(synth.queries_box(N, Q, 3)).cuda()
+    cp = ndg.CullParams(8, torch.as_tensor(synth.projections(N, 8, 4)).cuda(), 1 / 255, 3.0, 64)
+    ev = ndg.Evaluator(gm, x, 256, cp)
+    ev.build(gm)
+    dy = torch.randn(Q, 3, device="cuda") / Q
+    direct = ev.backward(gm, dy)
+    y_direct = ev.forward(gm)
+    names = ["mean", "theta", "alpha_raw", "color_raw", "u_theta", "m_u", "c_alpha_raw",
+             "c_color_raw"]
+    for n in names:
+        getattr(gm, n).requires_grad_(True)
+    y = evaluate(ev, gm)
+    assert torch.equal(y.detach(), y_direct)
+    y.backward(dy)
+    for n in names:
+        assert torch.equal(getattr(gm, n).grad[:G], getattr(direct, n)[:G]), n
+
+
+def test_fit_reduces_loss_and_refines(ndg):
+    """A small fit toward a ground-truth mixture: the loss falls, the step
+    counter advances, refinement adds children and materialises the ones
+    that grew (Section 3.3)."""
+    import torch
+    from paper_2405_20067_gb300.train import Trainer
+    N, G, Q = 6, 400, 8192
+    gt = ndg.Mixture.from_arrays(N, synth.mixture(N, 100, 50))
+    x = torch.as_tensor(synth.queries_box(N, Q, 51)).cuda()
+    cp_gt = ndg.CullParams(0, None, 0.0, 3.0, 1)
+    evg = ndg.Evaluator(gt, x, 256, cp_gt, E_cap=64 * 100 + 16)
+    evg.build(gt)
+    target = evg.forward(gt).clone()
+    start = synth.mixture(N, G, 52)
+    gm = ndg.Mixture.from_arrays(N, start, G_cap=2 * G)
+    cp = ndg.CullParams(8, torch.as_tensor(synth.projections(N, 8, 53)).cuda(), 0.0, 3.0, 64)
+    tr = Trainer(gm, x, target, 256, cp, lr=1e-2, t=0.01, phase=20)
+    losses = []
+    for i in range(60):
+        losses.append(float(tr.step().item()))
+        if tr.iteration % 20 == 0:
+            tr.check()
+    assert tr.step_dev.item() == 60
+    assert losses[-1] < 0.7 * losses[0], (losses[0], losses[-1])
+    assert tr.mix.has_children
+    assert tr.mix.G >= G
+    assert ndg.read_status(tr.ev.ws) == 0
