@@ -58,7 +58,9 @@ typedef enum {
   NDG_ERR_CUDA = 3,        /* a CUDA launch or copy failed               */
   NDG_ERR_NUMERIC = 4,     /* non-finite value in the parameters         */
   NDG_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out         */
-  NDG_ERR_WORKSPACE = 6    /* ws smaller than ndg_workspace_size()       */
+  NDG_ERR_WORKSPACE = 6,   /* ws smaller than ndg_workspace_size()       */
+  NDG_ERR_SCRATCH_LIMIT = 7 /* input larger than ndg_forward_noalloc's
+                               fixed scratch (NDG_NOALLOC_SCRATCH_BYTES)  */
 } ndg_status;
 
 #define NDG_MAX_N 12      /* dimensions                                  */
@@ -190,6 +192,28 @@ ndg_status ndg_densify(ndg_mixture* mix, float a_thr, float a_child0,
                        const float* noise, ndg_mixture* m1, ndg_mixture* m2,
                        int* G_new_dev, void* ws, size_t ws_bytes,
                        ndg_stream stream, ndg_trace* trace);
+
+/* ndg_forward without a workspace, for callers that cannot allocate device
+ * memory (for example a plugin inside a host application whose allocator
+ * owns the whole device budget, or a per-frame callback that cannot afford
+ * the device synchronisation an allocation may cause).  The paper has no
+ * counterpart; it is a deployment convenience.  Same result as ndg_forward
+ * (mode NDG_MODE_FP32) on the same inputs; the caller still owns mix, q,
+ * cull and y.  Its scratch (the prepared records, Ge * R * 4 bytes with
+ * Ge = G (1 + has_children) and R = N(N+1)/2 + N + 3 rounded up to a
+ * multiple of 4) lives in one static device array of
+ * NDG_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * exit; larger mixtures return NDG_ERR_SCRATCH_LIMIT before anything runs
+ * (N = 6: up to 131072 evaluated Gaussians; N = 10: up to 61680).  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race
+ * and must be serialised by the caller.  Device-side status (non-finite
+ * parameters) is not reported by this variant.  Calls nothing that
+ * allocates. */
+#define NDG_NOALLOC_SCRATCH_BYTES (16 << 20)
+ndg_status ndg_forward_noalloc(const ndg_mixture* mix, const ndg_queries* q,
+                               const ndg_cull* cull, float* y, ndg_stream stream);
 
 /* Synchronises `stream`, copies the workspace status word to *device_status
  * (an ndg_status value) and clears it. */

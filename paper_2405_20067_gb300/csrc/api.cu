@@ -532,6 +532,7 @@ const char* ndg_status_string(int status) {
     case NDG_ERR_NUMERIC: return "non-finite parameter";
     case NDG_ERR_TIMEOUT: return "device wait timed out";
     case NDG_ERR_WORKSPACE: return "workspace too small";
+    case NDG_ERR_SCRATCH_LIMIT: return "input exceeds the fixed no-allocation scratch";
     default: return "unknown status";
   }
 }

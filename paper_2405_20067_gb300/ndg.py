@@ -86,7 +86,9 @@ def _tr(trace):
 
 
 EXPORTS = ["ndg_workspace_size", "ndg_build_cull", "ndg_forward", "ndg_loss_l2", "ndg_backward",
-           "ndg_adam", "ndg_densify", "ndg_read_status", "ndg_status_string", "ndg_version"]
+           "ndg_adam", "ndg_densify", "ndg_read_status", "ndg_status_string", "ndg_version",
+           "ndg_forward_noalloc"]
+NDG_ERR_SCRATCH_LIMIT = 7
 
 
 def lib():
@@ -110,12 +112,13 @@ def lib():
         L.ndg_adam.argtypes = [M, M, M, M, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                ctypes.c_float, _P, TR]
         L.ndg_densify.argtypes = [M, ctypes.c_float, ctypes.c_float, _P, M, M, _P, _P, sz, _P, TR]
+        L.ndg_forward_noalloc.argtypes = [M, Qp, C, _P, _P]
         L.ndg_read_status.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_int)]
         L.ndg_status_string.argtypes = [ctypes.c_int]
         L.ndg_status_string.restype = ctypes.c_char_p
         L.ndg_version.restype = ctypes.c_int
         for name in ["ndg_build_cull", "ndg_forward", "ndg_loss_l2", "ndg_backward", "ndg_adam",
-                     "ndg_densify", "ndg_read_status"]:
+                     "ndg_densify", "ndg_read_status", "ndg_forward_noalloc"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -275,6 +278,15 @@ def forward(mix: Mixture, x: torch.Tensor, tile: int, cull: Cull, y: torch.Tenso
     _check(lib().ndg_forward(ctypes.byref(mix.c()), ctypes.byref(queries_c(x, tile)),
                              ctypes.byref(cull.c()), mode, _ptr(y), _ptr(ws), ws.numel(),
                              _stream(stream), _tr(trace)), "ndg_forward")
+
+
+def forward_noalloc(mix: Mixture, x: torch.Tensor, tile: int, cull: Cull, y: torch.Tensor,
+                    stream=None):
+    """ndg_forward_noalloc: the evaluation without a workspace, for callers
+    that cannot allocate device memory (see include/ndg.h)."""
+    _check(lib().ndg_forward_noalloc(ctypes.byref(mix.c()), ctypes.byref(queries_c(x, tile)),
+                                     ctypes.byref(cull.c()), _ptr(y), _stream(stream)),
+           "ndg_forward_noalloc")
 
 
 def loss_l2(y: torch.Tensor, target: torch.Tensor, dy: torch.Tensor, loss: torch.Tensor,
