@@ -34,10 +34,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "culled fwd+bwd Gaussian-query pairs/s and N=10 1080p render ms, vs plain FP32"
 UNIT = "pairs/s"
-N_DIM, G, Q, K_PROJ, TILE, BUCKETS = 6, 100_000, 1 << 20, 16, 256, 64
+N_DIM, K_PROJ, TILE, BUCKETS = 6, 16, 256, 64
 CUTOFF = 1.0 / 255.0
-WORKLOAD = (f"N={N_DIM} culled fit step: {G} Gaussians (+{G} children at brightness t/10), "
-            f"Q=2^20 Morton-tiled queries, tile {TILE}, k={K_PROJ} projections, "
+# the headline workload and a small case of the same density for profiling
+WORKLOADS = {"fit_n6": (100_000, 1 << 20), "small_n6": (12_500, 1 << 17)}
+G, Q = WORKLOADS["fit_n6"]
+
+
+def workload_name(g, q):
+    return (f"N={N_DIM} culled fit step: {g} Gaussians (+{g} children at brightness t/10), "
+            f"Q=2^{q.bit_length() - 1} Morton-tiled queries, tile {TILE}, k={K_PROJ} projections, "
             f"cutoff 1/255, {BUCKETS} buckets, Adam lr 1e-3")
 
 
@@ -121,7 +127,7 @@ class ClockSampler:
 def build_workload(device):
     import torch
     from paper_2405_20067_gb300 import ndg, synth
-    c = synth.config1()
+    c = synth.config1(G=G, Q=Q)
     mix = c["mix"]
     ch = synth.children(N_DIM, G, 11, spread=0.05, brightness=(0.0009, 0.0011))
     gm = ndg.Mixture.from_arrays(N_DIM, mix, ch, G_cap=G + G // 10, device=device)
@@ -189,7 +195,7 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2405_20067_gb300 import synth
-    c = synth.config1()
+    c = synth.config1(G=G, Q=Q)
     ch = synth.children(N_DIM, G, 11, spread=0.05, brightness=(0.0009, 0.0011))
     vals = []
     for i in range(args.warmup + args.steps):
@@ -202,7 +208,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
+           "data": "synthetic", "config": {"workload": workload_name(G, Q), "l2": "n/a (host)"},
            "cpu_baseline": cb,
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -215,7 +221,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="fit_n6", choices=sorted(WORKLOADS),
+                    help="fit_n6: the headline workload; small_n6: 1/8 of it for profiling")
     args = ap.parse_args()
+    global G, Q
+    G, Q = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args)
         return
@@ -311,7 +321,7 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "pairs_per_step": mean_pairs,
+           "config": {"workload": workload_name(G, Q), "pairs_per_step": mean_pairs,
                       "candidates_per_step": int(tr.ev.cull.E()),
                       "l2": "256 MB buffer written between timed steps (untimed)",
                       "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
