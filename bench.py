@@ -138,6 +138,58 @@ def build_workload(device):
     return c, ch, gm, x, target, cp
 
 
+RENDER = {"N": 10, "G": 500_000, "W": 1920, "H": 1080, "k": 16, "buckets": 64}
+
+
+def render_n10_1080p(device, steps: int, warmup: int, flush):
+    """Second metric: one 1920 x 1080 frame (16 x 16 pixel tiles, 8160 tiles,
+    the last tile row half full) of 10-D surface queries against 500,000
+    10-D Gaussians: cull + forward (S1-S4), ms per frame."""
+    import torch
+    from paper_2405_20067_gb300 import ndg, synth
+    r = RENDER
+    mix = synth.mixture(r["N"], r["G"], 2)
+    gm = ndg.Mixture.from_arrays(r["N"], mix, device=device)
+    x = torch.as_tensor(synth.queries_frame(r["N"], r["W"], r["H"], 3)).to(device)
+    proj = torch.as_tensor(synth.projections(r["N"], r["k"], 4)).to(device)
+    cp = ndg.CullParams(r["k"], proj, CUTOFF, 3.0, r["buckets"])
+    ev = ndg.Evaluator(gm, x, TILE, cp, E_cap=1 << 24, backward=False)
+    E = ev.build(gm)
+    y = torch.empty(x.shape[0], 3, dtype=torch.float32, device=device)
+    tc, tf = ndg.Trace(), ndg.Trace()
+
+    def frame(trace_c=None, trace_f=None):
+        ndg.build_cull(gm, x, TILE, cp, ev.cull, ev.ws, trace=trace_c)
+        ndg.forward(gm, x, TILE, ev.cull, y, ev.ws, trace=trace_f)
+
+    for _ in range(warmup):
+        frame()
+    ms, cull_ms, fwd_ms, launches = [], [], [], 0
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tc.c.launches = tf.c.launches = 0
+        a.record()
+        frame(tc, tf)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+        cull_ms.append(tc.ms())
+        fwd_ms.append(tf.ms())
+        launches += tc.launches + tf.launches
+    assert ndg.read_status(ev.ws) == ndg.NDG_OK
+    pairs = pairs_of(ev.cull, x.shape[0], TILE)
+    fwd_f, _ = flops_per_pair(r["N"])
+    med = statistics.median(fwd_ms)
+    return {"metric": "N=10 1080p render ms", "value": statistics.median(ms), "unit": "ms",
+            "higher_is_better": False, "form": "FP32 centred (plain FP32 form)",
+            "workload": f"{r['W']}x{r['H']} frame, 16x16 tiles, N=10, {r['G']} Gaussians, "
+                        f"k={r['k']}, cutoff 1/255",
+            "candidates": E, "pairs": pairs, "fwd_kernel_ms": med,
+            "fwd_tflops": round(pairs * fwd_f / (med / 1e3) / 1e12, 3),
+            "cull_fill_kernel_ms": statistics.median(cull_ms), "gpu_launches": launches}
+
+
 def pairs_of(cull, Qn, tile):
     import torch
     offs = cull.offsets
@@ -221,6 +273,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-render", action="store_true", help="skip the N=10 1080p render metric")
     ap.add_argument("--workload", default="fit_n6", choices=sorted(WORKLOADS),
                     help="fit_n6: the headline workload; small_n6: 1/8 of it for profiling")
     args = ap.parse_args()
@@ -327,6 +380,8 @@ def main():
                       "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
            "roofline": roofline, "kernels_ms": kernels, "gpu_launches": launches,
            "e2e": e2e, "clocks": clocks}
+    if not args.no_render and args.workload == "fit_n6":
+        out["render"] = render_n10_1080p(device, max(3, args.steps // 2), 3, flush)
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(c, ch)
     print(json.dumps(out), flush=True)

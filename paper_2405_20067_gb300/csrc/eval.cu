@@ -20,56 +20,156 @@
 
 namespace ndg {
 
-// ---- forward ----------------------------------------------------------------
+// ---- tile centre ---------------------------------------------------------------
+// Midpoint of the tile's bounding box (per dimension), computed by the CTA:
+// the kernels evaluate z = M (x - c) - M (m - c), which keeps the products
+// M x small (x - c is bounded by the tile) while giving the same z.
 template <int N>
-__global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
-  constexpr int P = tri(N), R = rec_floats(N), R4 = R / 4;
-  constexpr int CH = 64;
-  __shared__ __align__(16) float srec[CH * R];
-  const long long t = blockIdx.x;
-  const long long q = t * a.tile + threadIdx.x;
-  const bool active = threadIdx.x < a.tile && q < a.Q;
-  float x[N];
+__device__ __forceinline__ void tile_centre(const float (&xa)[N], bool va, const float (&xb)[N],
+                                            bool vb, float* __restrict__ sred,
+                                            float* __restrict__ sctr) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-  for (int d = 0; d < N; ++d) x[d] = active ? a.x[q * N + d] : 0.0f;
+  for (int d = 0; d < N; ++d) {
+    float lo = INFINITY, hi = -INFINITY;
+    if (va) { lo = xa[d]; hi = xa[d]; }
+    if (vb) { lo = fminf(lo, xb[d]); hi = fmaxf(hi, xb[d]); }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+      sred[(warp * N + d) * 2] = lo;
+      sred[(warp * N + d) * 2 + 1] = hi;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < N) {
+    float lo = INFINITY, hi = -INFINITY;
+    for (int w = 0; w < nw; ++w) {
+      lo = fminf(lo, sred[(w * N + threadIdx.x) * 2]);
+      hi = fmaxf(hi, sred[(w * N + threadIdx.x) * 2 + 1]);
+    }
+    sctr[threadIdx.x] = (lo <= hi) ? 0.5f * (lo + hi) : 0.0f;
+  }
+  __syncthreads();
+}
+
+// z' = kappa z with kappa = sqrt(log2(e) / 2): then exp(-|z|^2 / 2) = 2^(-|z'|^2).
+constexpr float kKappa = 0.84932180028801904272f;
+constexpr float kInvKappa = 1.17741002251547469101f;
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 ex2_f2(float2 v) { return make_float2(ex2_approx(v.x), ex2_approx(v.y)); }
+
+// ---- forward ----------------------------------------------------------------
+// One CTA of 128 threads per tile, two queries per thread; candidates are
+// processed two at a time as the two lanes of packed FP32x2 instructions,
+// their records interleaved in shared memory: (kappa M, -kappa M (m - c), w).
+template <int N>
+__global__ void __launch_bounds__(128) fwd_kernel(FwdArgs a) {
+  constexpr int P = tri(N), R = rec_floats(N), R4 = R / 4;
+  constexpr int RR = (2 * (P + N + 3) + 3) / 4 * 4;  // floats per candidate pair
+  constexpr int CH = 64;                              // candidates per stage
+  __shared__ __align__(16) float spair[CH / 2 * RR];
+  __shared__ float sred[4 * N * 2];
+  __shared__ float sctr[N];
+  const long long t = blockIdx.x;
+  const int tid = threadIdx.x;
+  const long long q0 = t * a.tile;
+  const int nq = (int)(a.Q - q0 < a.tile ? a.Q - q0 : a.tile);
+  const bool va = tid < nq, vb = tid + 128 < nq;
+  float xa[N], xb[N];
+#pragma unroll
+  for (int d = 0; d < N; ++d) {
+    xa[d] = va ? a.x[(q0 + tid) * N + d] : 0.0f;
+    xb[d] = vb ? a.x[(q0 + tid + 128) * N + d] : 0.0f;
+  }
+  tile_centre<N>(xa, va, xb, vb, sred, sctr);
+  float2 xa2[N], xb2[N];
+#pragma unroll
+  for (int d = 0; d < N; ++d) {
+    xa2[d] = f2(xa[d] - sctr[d]);
+    xb2[d] = f2(xb[d] - sctr[d]);
+  }
+  float2 acca[3] = {f2(0.f), f2(0.f), f2(0.f)}, accb[3] = {f2(0.f), f2(0.f), f2(0.f)};
   const long long beg = a.offsets[t], end = a.offsets[t + 1];
-  float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f;
   for (long long c0 = beg; c0 < end; c0 += CH) {
     const int n = (int)(end - c0 < CH ? end - c0 : CH);
-    for (int idx = threadIdx.x; idx < n * R4; idx += blockDim.x) {
-      const int row = idx / R4, col = idx - row * R4;
-      const int g = a.ids[c0 + row];
-      // an index outside this mixture (a stale list) reads as a zero-weight row
-      reinterpret_cast<float4*>(srec)[idx] =
-          (unsigned)g < (unsigned)a.Ge
-              ? __ldg(reinterpret_cast<const float4*>(a.rec) + (size_t)g * R4 + col)
-              : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    }
-    __syncthreads();
-    for (int j = 0; j < n; ++j) {
-      const float* r = srec + j * R;
-      float d[N];
+    if (tid < CH) {
+      // stage candidate tid: scaled M, -kappa M (m - c), w (zeros past the end)
+      float M[P], m[N], w[3];
+      const int g = tid < n ? a.ids[c0 + tid] : -1;
+      if ((unsigned)g < (unsigned)a.Ge) {
+        const float4* src = reinterpret_cast<const float4*>(a.rec) + (size_t)g * R4;
+        float buf[R];
 #pragma unroll
-      for (int i = 0; i < N; ++i) d[i] = x[i] - r[P + i];
-      float s = 0.0f;
+        for (int i = 0; i < R4; ++i) {
+          float4 v = __ldg(src + i);
+          buf[4 * i] = v.x; buf[4 * i + 1] = v.y; buf[4 * i + 2] = v.z; buf[4 * i + 3] = v.w;
+        }
+#pragma unroll
+        for (int i = 0; i < P; ++i) M[i] = kKappa * buf[i];
+#pragma unroll
+        for (int i = 0; i < N; ++i) m[i] = buf[P + i] - sctr[i];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) w[i] = buf[P + N + i];
+      } else {
+#pragma unroll
+        for (int i = 0; i < P; ++i) M[i] = 0.0f;
+#pragma unroll
+        for (int i = 0; i < N; ++i) m[i] = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) w[i] = 0.0f;
+      }
+      float* dst = spair + (tid >> 1) * RR + (tid & 1);
+#pragma unroll
+      for (int i = 0; i < P; ++i) dst[2 * i] = M[i];
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        float z = 0.0f;
+        float bi = 0.0f;
 #pragma unroll
-        for (int k = 0; k <= i; ++k) z = fmaf(r[tri(i) + k], d[k], z);
-        s = fmaf(z, z, s);
+        for (int k = 0; k <= i; ++k) bi = fmaf(M[tri(i) + k], m[k], bi);
+        dst[2 * (P + i)] = -bi;
       }
-      const float e = ex2_approx(s * kNegHalfLog2e);
-      acc0 = fmaf(r[P + N + 0], e, acc0);
-      acc1 = fmaf(r[P + N + 1], e, acc1);
-      acc2 = fmaf(r[P + N + 2], e, acc2);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) dst[2 * (P + N + i)] = w[i];
+    }
+    __syncthreads();
+    const int npairs = (n + 1) >> 1;
+    for (int p = 0; p < npairs; ++p) {
+      const float2* r = reinterpret_cast<const float2*>(spair + p * RR);
+      float2 sa = f2(0.f), sb = f2(0.f);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        float2 za = r[P + i], zb = r[P + i];
+#pragma unroll
+        for (int k = 0; k <= i; ++k) {
+          const float2 mik = r[tri(i) + k];
+          za = __ffma2_rn(mik, xa2[k], za);
+          zb = __ffma2_rn(mik, xb2[k], zb);
+        }
+        sa = __ffma2_rn(make_float2(-za.x, -za.y), za, sa);
+        sb = __ffma2_rn(make_float2(-zb.x, -zb.y), zb, sb);
+      }
+      const float2 ea = ex2_f2(sa), eb = ex2_f2(sb);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float2 wc = r[P + N + c];
+        acca[c] = __ffma2_rn(wc, ea, acca[c]);
+        accb[c] = __ffma2_rn(wc, eb, accb[c]);
+      }
     }
     __syncthreads();
   }
-  if (active) {
-    a.y[q * 3 + 0] = acc0;
-    a.y[q * 3 + 1] = acc1;
-    a.y[q * 3 + 2] = acc2;
+  if (va) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a.y[(q0 + tid) * 3 + c] = acca[c].x + acca[c].y;
+  }
+  if (vb) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a.y[(q0 + tid + 128) * 3 + c] = accb[c].x + accb[c].y;
   }
 }
 
@@ -110,90 +210,153 @@ __global__ void __launch_bounds__(LOSS_BLOCKS) loss_final_kernel(const double* _
 }
 
 // ---- backward partials ------------------------------------------------------------
+// One CTA of 128 threads per tile; each thread owns two candidates (the two
+// lanes of packed FP32x2 instructions) and loops over the tile's queries,
+// read from shared memory as (x - c, dy) duplicated into both lanes.  With
+// z' = kappa z: beta = e sum_c dy_c w_c, and the partial record of an entry
+// is [sum beta z d^T (lower), sum beta z, sum dy e], formed from
+// sum beta z' (x - c)^T - (sum beta z') (m - c)^T at the end.  Records go to
+// the entry's Gaussian-major slot slot[c], so that the per-Gaussian sums read
+// contiguous memory.
 template <int N>
-__global__ void __launch_bounds__(256, 1) bwd_kernel(BwdArgs a) {
-  constexpr int P = tri(N), R = rec_floats(N), RP = part_floats(N);
-  constexpr int QS = (N + 3 + 3) / 4 * 4;  // x (N) and dy (3) per query, 16-byte rows
+__global__ void __launch_bounds__(128) bwd_kernel(BwdArgs a) {
+  constexpr int P = tri(N), R = rec_floats(N), R4 = R / 4, RP = part_floats(N);
+  constexpr int QS = (2 * (N + 3) + 3) / 4 * 4;  // floats per query: (x - c, dy) x 2 lanes
   __shared__ __align__(16) float sq[NDG_MAX_TILE * QS];
+  __shared__ float sred[4 * N * 2];
+  __shared__ float sctr[N];
   const long long t = blockIdx.x;
+  const int tid = threadIdx.x;
   const long long q0 = t * a.tile;
   const int nq = (int)(a.Q - q0 < a.tile ? a.Q - q0 : a.tile);
-  for (int i = threadIdx.x; i < nq * QS; i += blockDim.x) {
-    const int qi = i / QS, c = i - qi * QS;
-    float v = 0.0f;
-    if (c < N) v = a.x[(q0 + qi) * N + c];
-    else if (c < N + 3) v = a.dy[(q0 + qi) * 3 + (c - N)];
-    sq[i] = v;
+  {
+    const bool va = tid < nq, vb = tid + 128 < nq;
+    float xa[N], xb[N];
+#pragma unroll
+    for (int d = 0; d < N; ++d) {
+      xa[d] = va ? a.x[(q0 + tid) * N + d] : 0.0f;
+      xb[d] = vb ? a.x[(q0 + tid + 128) * N + d] : 0.0f;
+    }
+    tile_centre<N>(xa, va, xb, vb, sred, sctr);
+    for (int h = 0; h < 2; ++h) {
+      const int qi = tid + 128 * h;
+      if (qi >= nq) continue;
+      float* row = sq + qi * QS;
+#pragma unroll
+      for (int d = 0; d < N; ++d) {
+        const float v = (h ? xb[d] : xa[d]) - sctr[d];
+        row[2 * d] = v;
+        row[2 * d + 1] = v;
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float v = a.dy[(q0 + qi) * 3 + c];
+        row[2 * (N + c)] = v;
+        row[2 * (N + c) + 1] = v;
+      }
+    }
   }
   __syncthreads();
   const long long beg = a.offsets[t], end = a.offsets[t + 1];
-  for (long long c0 = beg; c0 < end; c0 += blockDim.x) {
-    const long long c = c0 + threadIdx.x;
-    const bool act = c < end;
-    float M[P], m[N], w[3];
-    const int gid = act ? a.ids[c] : -1;
-    if (act && (unsigned)gid < (unsigned)a.Ge) {
-      const float* r = a.rec + (size_t)gid * R;
+  for (long long c0 = beg; c0 < end; c0 += 256) {
+    const long long cid[2] = {c0 + tid, c0 + 128 + tid};
+    float2 M2[P], b2[N], w2[3];
+    float mt[2][N];  // m - c of both candidates (for the final product)
 #pragma unroll
-      for (int i = 0; i < P; ++i) M[i] = r[i];
+    for (int h = 0; h < 2; ++h) {
+      const int g = cid[h] < end ? a.ids[cid[h]] : -1;
+      float buf[R];
+      if ((unsigned)g < (unsigned)a.Ge) {
+        const float4* src = reinterpret_cast<const float4*>(a.rec) + (size_t)g * R4;
 #pragma unroll
-      for (int i = 0; i < N; ++i) m[i] = r[P + i];
+        for (int i = 0; i < R4; ++i) {
+          float4 v = __ldg(src + i);
+          buf[4 * i] = v.x; buf[4 * i + 1] = v.y; buf[4 * i + 2] = v.z; buf[4 * i + 3] = v.w;
+        }
+      } else {
 #pragma unroll
-      for (int i = 0; i < 3; ++i) w[i] = r[P + N + i];
-    } else {
+        for (int i = 0; i < R; ++i) buf[i] = 0.0f;
+      }
 #pragma unroll
-      for (int i = 0; i < P; ++i) M[i] = 0.0f;
+      for (int i = 0; i < P; ++i) {
+        const float v = kKappa * buf[i];
+        if (h) M2[i].y = v; else M2[i].x = v;
+      }
 #pragma unroll
-      for (int i = 0; i < N; ++i) m[i] = 0.0f;
+      for (int i = 0; i < N; ++i) mt[h][i] = buf[P + i] - sctr[i];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) w[i] = 0.0f;
+      for (int i = 0; i < 3; ++i) {
+        if (h) w2[i].y = buf[P + N + i]; else w2[i].x = buf[P + N + i];
+      }
     }
-    float GM[P], Gz[N], Gw[3];
 #pragma unroll
-    for (int i = 0; i < P; ++i) GM[i] = 0.0f;
+    for (int i = 0; i < N; ++i) {
+      float ba = 0.0f, bb = 0.0f;
 #pragma unroll
-    for (int i = 0; i < N; ++i) Gz[i] = 0.0f;
+      for (int k = 0; k <= i; ++k) {
+        ba = fmaf(M2[tri(i) + k].x, mt[0][k], ba);
+        bb = fmaf(M2[tri(i) + k].y, mt[1][k], bb);
+      }
+      b2[i] = make_float2(-ba, -bb);
+    }
+    float2 GM2[P], Gz2[N], Gw2[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) Gw[i] = 0.0f;
+    for (int i = 0; i < P; ++i) GM2[i] = f2(0.f);
+#pragma unroll
+    for (int i = 0; i < N; ++i) Gz2[i] = f2(0.f);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Gw2[i] = f2(0.f);
     for (int qi = 0; qi < nq; ++qi) {
-      const float* qq = sq + qi * QS;
-      float d[N], z[N];
+      const float2* qq = reinterpret_cast<const float2*>(sq + qi * QS);
+      float2 x2[N], z2[N];
 #pragma unroll
-      for (int i = 0; i < N; ++i) d[i] = qq[i] - m[i];
-      float s = 0.0f;
+      for (int d = 0; d < N; ++d) x2[d] = qq[d];
+      float2 s2 = f2(0.f);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        float zi = 0.0f;
+        float2 z = b2[i];
 #pragma unroll
-        for (int k = 0; k <= i; ++k) zi = fmaf(M[tri(i) + k], d[k], zi);
-        z[i] = zi;
-        s = fmaf(zi, zi, s);
+        for (int k = 0; k <= i; ++k) z = __ffma2_rn(M2[tri(i) + k], x2[k], z);
+        z2[i] = z;
+        s2 = __ffma2_rn(make_float2(-z.x, -z.y), z, s2);
       }
-      const float e = ex2_approx(s * kNegHalfLog2e);
-      const float g0 = qq[N], g1 = qq[N + 1], g2 = qq[N + 2];
-      Gw[0] = fmaf(g0, e, Gw[0]);
-      Gw[1] = fmaf(g1, e, Gw[1]);
-      Gw[2] = fmaf(g2, e, Gw[2]);
-      const float beta = e * fmaf(g0, w[0], fmaf(g1, w[1], g2 * w[2]));
+      const float2 e2 = ex2_f2(s2);
+      const float2 g0 = qq[N], g1 = qq[N + 1], g2 = qq[N + 2];
+      Gw2[0] = __ffma2_rn(g0, e2, Gw2[0]);
+      Gw2[1] = __ffma2_rn(g1, e2, Gw2[1]);
+      Gw2[2] = __ffma2_rn(g2, e2, Gw2[2]);
+      float2 tt = __fmul2_rn(g0, w2[0]);
+      tt = __ffma2_rn(g1, w2[1], tt);
+      tt = __ffma2_rn(g2, w2[2], tt);
+      const float2 beta = __fmul2_rn(e2, tt);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        const float bz = beta * z[i];
-        Gz[i] += bz;
+        const float2 bz = __fmul2_rn(beta, z2[i]);
+        Gz2[i] = __fadd2_rn(Gz2[i], bz);
 #pragma unroll
-        for (int k = 0; k <= i; ++k) GM[tri(i) + k] = fmaf(bz, d[k], GM[tri(i) + k]);
+        for (int k = 0; k <= i; ++k) GM2[tri(i) + k] = __ffma2_rn(bz, x2[k], GM2[tri(i) + k]);
       }
     }
-    if (act) {
-      float* out = a.part + (size_t)c * RP;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (cid[h] >= end) continue;
       float buf[RP];
 #pragma unroll
-      for (int i = 0; i < P; ++i) buf[i] = GM[i];
+      for (int i = 0; i < N; ++i) {
+        const float gz = h ? Gz2[i].y : Gz2[i].x;
 #pragma unroll
-      for (int i = 0; i < N; ++i) buf[P + i] = Gz[i];
+        for (int k = 0; k <= i; ++k) {
+          const float gm = h ? GM2[tri(i) + k].y : GM2[tri(i) + k].x;
+          buf[tri(i) + k] = kInvKappa * fmaf(-gz, mt[h][k], gm);
+        }
+        buf[P + i] = kInvKappa * gz;
+      }
 #pragma unroll
-      for (int i = 0; i < 3; ++i) buf[P + N + i] = Gw[i];
+      for (int c = 0; c < 3; ++c) buf[P + N + c] = h ? Gw2[c].y : Gw2[c].x;
 #pragma unroll
       for (int i = P + N + 3; i < RP; ++i) buf[i] = 0.0f;
+      const long long slot = a.slot ? (long long)a.slot[cid[h]] : cid[h];
+      float* out = a.part + (size_t)slot * RP;
 #pragma unroll
       for (int i = 0; i < RP; i += 4)
         *reinterpret_cast<float4*>(out + i) = make_float4(buf[i], buf[i + 1], buf[i + 2], buf[i + 3]);
@@ -202,19 +365,47 @@ __global__ void __launch_bounds__(256, 1) bwd_kernel(BwdArgs a) {
 }
 
 // ---- per-Gaussian sums of the partial records (Gaussian-major, fixed order) --
+// One warp per evaluated Gaussian; its records are contiguous (slots
+// goff[e] .. goff[e+1]).  Lanes are split into groups of RP/4 (one float4
+// column each) that take every G-th record; the groups' sums are combined
+// in group order, so the result does not depend on scheduling.
 __global__ void __launch_bounds__(256) segsum_kernel(const float* __restrict__ part, int RP,
-                                                     const int32_t* __restrict__ gidx,
                                                      const long long* __restrict__ goff, int Ge,
                                                      float* __restrict__ gsum) {
-  const long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (e >= Ge) return;
-  const long long b = goff[e], en = goff[e + 1];
-  for (int c = lane; c < RP; c += 32) {
-    float acc = 0.0f;
-    for (long long j = b; j < en; ++j) acc += part[(size_t)gidx[j] * RP + c];
-    gsum[(size_t)e * RP + c] = acc;
+  __shared__ float4 sh[8][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long e = (long long)blockIdx.x * 8 + warp;
+  const int RP4 = RP >> 2;
+  const int G = 32 / RP4 > 0 ? 32 / RP4 : 1;
+  const int grp = lane / RP4, col = lane - grp * RP4;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (e < Ge && grp < G && col < RP4) {
+    const long long b = goff[e], en = goff[e + 1];
+    const float4* src = reinterpret_cast<const float4*>(part);
+    for (long long j = b + grp; j < en; j += G) {
+      const float4 v = __ldg(src + j * RP4 + col);
+      acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    }
   }
+  sh[warp][lane] = acc;
+  __syncwarp();
+  if (e < Ge && lane < RP4) {
+    float4 s = sh[warp][lane];
+    for (int g = 1; g < G; ++g) {
+      const float4 v = sh[warp][g * RP4 + lane];
+      s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+    }
+    reinterpret_cast<float4*>(gsum)[e * RP4 + lane] = s;
+  }
+}
+
+// Entry -> Gaussian-major slot: slot[gidx[p]] = p.
+__global__ void invert_perm_kernel(const int32_t* __restrict__ gidx, long long n_cap,
+                                   const long long* __restrict__ n_dev, int32_t* __restrict__ slot) {
+  long long n = *n_dev < n_cap ? *n_dev : n_cap;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x)
+    slot[gidx[p]] = (int32_t)p;
 }
 
 // ---- chain rule to the raw parameters --------------------------------------------
@@ -397,7 +588,7 @@ __global__ void __launch_bounds__(128) chain_kernel(ChainArgs a) {
 
 int launch_fwd(int N, const FwdArgs& a, long long T, cudaStream_t s) {
   if (T <= 0) return 0;
-#define L_FWD(n) fwd_kernel<n><<<(unsigned)T, 256, 0, s>>>(a)
+#define L_FWD(n) fwd_kernel<n><<<(unsigned)T, 128, 0, s>>>(a)
   NDG_SWITCH_N(N, L_FWD)
 #undef L_FWD
   return 1;
@@ -413,17 +604,24 @@ int launch_loss(const float* y, const float* target, float* dy, long long n, dou
 
 int launch_bwd(int N, const BwdArgs& a, long long T, cudaStream_t s) {
   if (T <= 0) return 0;
-#define L_BWD(n) bwd_kernel<n><<<(unsigned)T, 256, 0, s>>>(a)
+#define L_BWD(n) bwd_kernel<n><<<(unsigned)T, 128, 0, s>>>(a)
   NDG_SWITCH_N(N, L_BWD)
 #undef L_BWD
   return 1;
 }
 
-int launch_segsum(const float* part, int RP, const int32_t* gidx, const long long* goff, int Ge,
-                  float* gsum, cudaStream_t s) {
+int launch_segsum(const float* part, int RP, const long long* goff, int Ge, float* gsum,
+                  cudaStream_t s) {
   if (Ge <= 0) return 0;
-  segsum_kernel<<<(unsigned)ceil_div<long long>((long long)Ge * 32, 256), 256, 0, s>>>(
-      part, RP, gidx, goff, Ge, gsum);
+  segsum_kernel<<<(unsigned)ceil_div<long long>(Ge, 8), 256, 0, s>>>(part, RP, goff, Ge, gsum);
+  return 1;
+}
+
+int launch_invert_perm(const int32_t* gidx, long long n_cap, const long long* n_dev, int32_t* slot,
+                       cudaStream_t s) {
+  long long blocks = ceil_div<long long>(n_cap > 0 ? n_cap : 1, 256);
+  if (blocks > 65535) blocks = 65535;
+  invert_perm_kernel<<<(unsigned)blocks, 256, 0, s>>>(gidx, n_cap, n_dev, slot);
   return 1;
 }
 

@@ -53,6 +53,7 @@ struct BwdArgs {
   const int* ids;
   const float* rec;
   int Ge;
+  const int32_t* slot;       // entry -> Gaussian-major slot, or null (entry order)
   float* part;               // [E_cap][part_floats(N)]
 };
 
@@ -106,8 +107,10 @@ int launch_fwd(int N, const FwdArgs& a, long long T, cudaStream_t s);
 int launch_loss(const float* y, const float* target, float* dy, long long n, double* part,
                  double* loss, cudaStream_t s);
 int launch_bwd(int N, const BwdArgs& a, long long T, cudaStream_t s);
-int launch_segsum(const float* part, int RP, const int32_t* gidx, const long long* goff, int Ge,
-                   float* gsum, cudaStream_t s);
+int launch_segsum(const float* part, int RP, const long long* goff, int Ge, float* gsum,
+                 cudaStream_t s);
+int launch_invert_perm(const int32_t* gidx, long long n_cap, const long long* n_dev, int32_t* slot,
+                       cudaStream_t s);
 int launch_chain(int N, const ChainArgs& a, cudaStream_t s);
 int launch_adam(const AdamArgs& a, cudaStream_t s);
 int launch_densify(int N, const DensifyArgs& a, cudaStream_t s);
