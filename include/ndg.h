@@ -141,6 +141,10 @@ ndg_status ndg_build_cull(const ndg_mixture* mix, const ndg_queries* q,
                           size_t ws_bytes, ndg_stream stream, ndg_trace* trace);
 
 #define NDG_MODE_FP32 0 /* centred form z = L^{-1}(x - m) on the FP32 pipe */
+#define NDG_MODE_TC 1   /* lifted quadratic form on the tensor cores: s =
+                           phi(x - c) . coef with phi = [x x^T (lower), x, 1],
+                           coef from A = V^-1, split TF32 (3 products), FP32
+                           accumulation; about 1e-5 relative on s's scale */
 
 /* Eq. 1 and Eq. 8: y [Q][3] = culled mixture sum at every query.  `cull`
  * must come from ndg_build_cull on the same mixture and queries. */

@@ -318,7 +318,7 @@ ndg_status ndg_forward(const ndg_mixture* mix, const ndg_queries* q, const ndg_c
                        ndg_trace* trace) {
   ndg_status st;
   if ((st = check_mix(mix)) || (st = check_queries(q)) || (st = check_cull(cull))) return st;
-  if (mode != NDG_MODE_FP32) return NDG_ERR_INVALID_ARG;
+  if (mode != NDG_MODE_FP32 && mode != NDG_MODE_TC) return NDG_ERR_INVALID_ARG;
   if (q->Q > 0 && !y) return NDG_ERR_INVALID_ARG;
   if (!ws || !aligned(ws, kAlign)) return NDG_ERR_INVALID_ARG;
   Sizes z = make_sizes(mix, q, nullptr, 0);
@@ -329,6 +329,7 @@ ndg_status ndg_forward(const ndg_mixture* mix, const ndg_queries* q, const ndg_c
   char* w = (char*)ws;
   PrepArgs pa = prep_args(mix);
   pa.rec = (float*)(w + c.rec);
+  pa.rec_kind = mode == NDG_MODE_TC ? 1 : 0;
   pa.status = &reinterpret_cast<WsHeader*>(w + c.header)->status;
   tr += launch_prep(mix->N, pa, s);
   FwdArgs fa{};
@@ -340,8 +341,9 @@ ndg_status ndg_forward(const ndg_mixture* mix, const ndg_queries* q, const ndg_c
   fa.rec = pa.rec;
   fa.Ge = pa.Ge;
   fa.y = y;
+  fa.status = pa.status;
   tr.begin();
-  tr += launch_fwd(mix->N, fa, z.T, s);
+  tr += mode == NDG_MODE_TC ? launch_fwd_tc(mix->N, fa, z.T, s) : launch_fwd(mix->N, fa, z.T, s);
   tr.end();
   return cuda_ok();
 }

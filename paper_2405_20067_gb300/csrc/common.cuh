@@ -51,4 +51,40 @@ __device__ __forceinline__ int clampi(int v, int a, int b) { return v < a ? a : 
 template <typename T>
 __host__ __device__ inline T ceil_div(T a, T b) { return (a + b - 1) / b; }
 
+// ---- tile centre ---------------------------------------------------------------
+// Midpoint of the tile's bounding box (per dimension), computed by the CTA:
+// the kernels evaluate z = M (x - c) - M (m - c), which keeps the products
+// M x small (x - c is bounded by the tile) while giving the same z.
+template <int N>
+__device__ __forceinline__ void tile_centre(const float (&xa)[N], bool va, const float (&xb)[N],
+                                            bool vb, float* __restrict__ sred,
+                                            float* __restrict__ sctr) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int d = 0; d < N; ++d) {
+    float lo = INFINITY, hi = -INFINITY;
+    if (va) { lo = xa[d]; hi = xa[d]; }
+    if (vb) { lo = fminf(lo, xb[d]); hi = fmaxf(hi, xb[d]); }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+      sred[(warp * N + d) * 2] = lo;
+      sred[(warp * N + d) * 2 + 1] = hi;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < N) {
+    float lo = INFINITY, hi = -INFINITY;
+    for (int w = 0; w < nw; ++w) {
+      lo = fminf(lo, sred[(w * N + threadIdx.x) * 2]);
+      hi = fmaxf(hi, sred[(w * N + threadIdx.x) * 2 + 1]);
+    }
+    sctr[threadIdx.x] = (lo <= hi) ? 0.5f * (lo + hi) : 0.0f;
+  }
+  __syncthreads();
+}
+
 }  // namespace ndg

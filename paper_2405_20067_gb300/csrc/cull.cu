@@ -201,8 +201,21 @@ __global__ void __launch_bounds__(128) prep_kernel(PrepArgs a) {
     }
     float* out = a.rec + (size_t)e * R;
     float buf[R];
+    if (a.rec_kind == 1) {
+      // A = V^-1 = M^T M (lower, packed): A_ij = sum_{k >= i} M_ki M_kj, j <= i
 #pragma unroll
-    for (int i = 0; i < P; ++i) buf[i] = (float)M[i];
+      for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+          double s = 0.0;
+#pragma unroll
+          for (int kk = i; kk < N; ++kk) s = fma(M[tri(kk) + i], M[tri(kk) + j], s);
+          buf[tri(i) + j] = (float)s;
+        }
+    } else {
+#pragma unroll
+      for (int i = 0; i < P; ++i) buf[i] = (float)M[i];
+    }
 #pragma unroll
     for (int i = 0; i < N; ++i) buf[P + i] = mf[i];
 #pragma unroll

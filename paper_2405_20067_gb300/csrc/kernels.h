@@ -11,6 +11,7 @@ struct PrepArgs {
   const float *mean, *theta, *alpha_raw, *color_raw;
   const float *u_theta, *m_u, *c_alpha_raw, *c_color_raw;
   float* rec;  // [Ge][rec_floats(N)] or null
+  int rec_kind;  // 0: M = L^-1 packed; 1: A = M^T M packed (lifted tensor-core form)
   // cull keys (when gkey or bin is set)
   int k, KP, B;
   const float* proj;
@@ -42,6 +43,7 @@ struct FwdArgs {
   const float* rec;          // [Ge][rec_floats(N)]
   int Ge;
   float* y;                  // [Q][3]
+  int* status;               // device status word (timeouts of bounded waits)
 };
 
 struct BwdArgs {
@@ -104,6 +106,8 @@ int launch_tile_keys(const float* tb, long long T, int k, int KP, int B, const f
 int launch_prep(int N, const PrepArgs& a, cudaStream_t s);
 int launch_cull_tile(int KP, const CullTileArgs& a, long long T, cudaStream_t s);
 int launch_fwd(int N, const FwdArgs& a, long long T, cudaStream_t s);
+int launch_fwd_tc(int N, const FwdArgs& a, long long T, cudaStream_t s);
+size_t fwd_tc_smem(int N);
 int launch_loss(const float* y, const float* target, float* dy, long long n, double* part,
                  double* loss, cudaStream_t s);
 int launch_bwd(int N, const BwdArgs& a, long long T, cudaStream_t s);

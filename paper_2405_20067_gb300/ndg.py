@@ -24,6 +24,7 @@ _lib = None
 NDG_OK = 0
 NDG_ERR_CAPACITY = 2
 NDG_MODE_FP32 = 0
+NDG_MODE_TC = 1
 MAX_N, MAX_K, MAX_BUCKETS, MAX_TILE = 12, 32, 255, 256
 _P = ctypes.c_void_p
 
@@ -371,10 +372,11 @@ class Evaluator:
             E = self.cull.E()
         return E
 
-    def forward(self, mix: Mixture, y: torch.Tensor | None = None) -> torch.Tensor:
+    def forward(self, mix: Mixture, y: torch.Tensor | None = None,
+                mode: int = NDG_MODE_FP32) -> torch.Tensor:
         if y is None:
             y = torch.empty(self.x.shape[0], 3, dtype=torch.float32, device=self.x.device)
-        forward(mix, self.x, self.tile, self.cull, y, self.ws)
+        forward(mix, self.x, self.tile, self.cull, y, self.ws, mode=mode)
         return y
 
     def backward(self, mix: Mixture, dy: torch.Tensor, grad: Mixture | None = None) -> Mixture:

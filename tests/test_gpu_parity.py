@@ -78,6 +78,36 @@ def test_cull_lists_bit_exact_and_forward(ndg, oracle, N, G, Q, tile, k, cutoff,
     assert ndg.read_status(ev.ws) == 0
 
 
+TC_CASES = [
+    # N, G, Q, tile, k, cutoff, B, children
+    (6, 2000, 20000, 256, 16, 1 / 255, 64, False),
+    (6, 900, 7000, 100, 8, 0.0, 64, True),
+    (10, 1200, 12288, 256, 16, 1 / 255, 128, False),
+    (10, 300, 3000, 17, 4, 0.0, 32, True),
+    (3, 500, 5000, 64, 2, 0.0, 32, False),
+    (1, 200, 2000, 256, 1, 1 / 255, 64, False),
+    (12, 400, 2000, 256, 24, 1 / 255, 16, False),
+]
+
+
+@pytest.mark.parametrize("N,G,Q,tile,k,cutoff,B,children", TC_CASES)
+def test_tc_forward_matches_oracle(ndg, oracle, N, G, Q, tile, k, cutoff, B, children):
+    """Lifted tensor-core form: within 1e-3 relative of the FP64 oracle on
+    outputs above 1e-3 (|a - b| / max(|b|, 1e-3) <= 1e-3)."""
+    seed = 500 + N + k
+    mix, ch, x = make_case(N, G, Q, seed, children)
+    gm, xt, proj, cp, ev, E = gpu_setup(ndg, N, mix, ch, x, tile, k, cutoff, 3.0, B, seed)
+    y = ev.forward(gm, mode=ndg.NDG_MODE_TC).cpu().numpy()
+    raw = oracle_raw(oracle, mix, ch)
+    L, m, w = oracle.activate(raw)
+    offs, ids = oracle.cull_contract(L, m, w, x.astype(np.float64), tile, proj, cutoff, 3.0, B)
+    assert E == offs[-1]
+    yo = oracle.eval(L, m, w, x.astype(np.float64), tile, offs, ids)
+    worst = assert_outputs_close(y, yo, rtol=1e-3, floor=1e-3, what="tensor-core forward")
+    print(f"N={N} tile={tile}: worst relative error {worst:.2e}")
+    assert ndg.read_status(ev.ws) == 0
+
+
 def test_dense_forward_config0(ndg, oracle):
     """N = 6, 1000 Gaussians, 16384 queries, no culling (k = 0)."""
     c = synth.config0()
