@@ -144,7 +144,8 @@ RENDER = {"N": 10, "G": 500_000, "W": 1920, "H": 1080, "k": 16, "buckets": 64}
 def render_n10_1080p(device, steps: int, warmup: int, flush):
     """Second metric: one 1920 x 1080 frame (16 x 16 pixel tiles, 8160 tiles,
     the last tile row half full) of 10-D surface queries against 500,000
-    10-D Gaussians: cull + forward (S1-S4), ms per frame."""
+    10-D Gaussians: cull + forward (S1-S4), ms per frame, for the lifted
+    tensor-core form (the value) and the plain FP32 form."""
     import torch
     from paper_2405_20067_gb300 import ndg, synth
     r = RENDER
@@ -157,37 +158,41 @@ def render_n10_1080p(device, steps: int, warmup: int, flush):
     E = ev.build(gm)
     y = torch.empty(x.shape[0], 3, dtype=torch.float32, device=device)
     tc, tf = ndg.Trace(), ndg.Trace()
+    out = {}
+    for form, mode in (("tc", ndg.NDG_MODE_TC), ("fp32", ndg.NDG_MODE_FP32)):
+        def frame(trace_c=None, trace_f=None):
+            ndg.build_cull(gm, x, TILE, cp, ev.cull, ev.ws, trace=trace_c)
+            ndg.forward(gm, x, TILE, ev.cull, y, ev.ws, mode=mode, trace=trace_f)
 
-    def frame(trace_c=None, trace_f=None):
-        ndg.build_cull(gm, x, TILE, cp, ev.cull, ev.ws, trace=trace_c)
-        ndg.forward(gm, x, TILE, ev.cull, y, ev.ws, trace=trace_f)
-
-    for _ in range(warmup):
-        frame()
-    ms, cull_ms, fwd_ms, launches = [], [], [], 0
-    for _ in range(steps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        tc.c.launches = tf.c.launches = 0
-        a.record()
-        frame(tc, tf)
-        b.record()
-        torch.cuda.synchronize()
-        ms.append(a.elapsed_time(b))
-        cull_ms.append(tc.ms())
-        fwd_ms.append(tf.ms())
-        launches += tc.launches + tf.launches
+        for _ in range(warmup):
+            frame()
+        ms, cull_ms, fwd_ms, launches = [], [], [], 0
+        n = steps if form == "tc" else max(2, steps // 2)
+        for _ in range(n):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            tc.c.launches = tf.c.launches = 0
+            a.record()
+            frame(tc, tf)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+            cull_ms.append(tc.ms())
+            fwd_ms.append(tf.ms())
+            launches += tc.launches + tf.launches
+        out[form] = {"ms": statistics.median(ms), "fwd_kernel_ms": statistics.median(fwd_ms),
+                     "cull_fill_kernel_ms": statistics.median(cull_ms), "gpu_launches": launches}
     assert ndg.read_status(ev.ws) == ndg.NDG_OK
     pairs = pairs_of(ev.cull, x.shape[0], TILE)
     fwd_f, _ = flops_per_pair(r["N"])
-    med = statistics.median(fwd_ms)
-    return {"metric": "N=10 1080p render ms", "value": statistics.median(ms), "unit": "ms",
-            "higher_is_better": False, "form": "FP32 centred (plain FP32 form)",
+    return {"metric": "N=10 1080p render ms", "value": out["tc"]["ms"], "unit": "ms",
+            "higher_is_better": False, "form": "lifted tensor-core forward",
+            "fp32_form_ms": out["fp32"]["ms"],
             "workload": f"{r['W']}x{r['H']} frame, 16x16 tiles, N=10, {r['G']} Gaussians, "
-                        f"k={r['k']}, cutoff 1/255",
-            "candidates": E, "pairs": pairs, "fwd_kernel_ms": med,
-            "fwd_tflops": round(pairs * fwd_f / (med / 1e3) / 1e12, 3),
-            "cull_fill_kernel_ms": statistics.median(cull_ms), "gpu_launches": launches}
+                        f"k={r['k']}, cutoff 1/255 (non-position dims uniform per pixel)",
+            "candidates": E, "pairs": pairs, "tc": out["tc"], "fp32": out["fp32"],
+            "fp32_fwd_tflops": round(pairs * fwd_f / (out["fp32"]["fwd_kernel_ms"] / 1e3) / 1e12, 3),
+            "tc_pairs_per_s": pairs / (out["tc"]["fwd_kernel_ms"] / 1e3)}
 
 
 def pairs_of(cull, Qn, tile):
@@ -266,6 +271,78 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_fit(form: str, steps: int, warmup: int, device: str, flush, world: int, e2e_steps: int):
+    """Times `steps` fit steps of the workload in one form ("tc": lifted
+    tensor-core forward; "fp32": plain FP32 forward); backward, cull, loss,
+    Adam and the refinement check are shared."""
+    import torch
+    from paper_2405_20067_gb300 import ndg
+    from paper_2405_20067_gb300.train import Trainer
+    import torch.distributed as dist
+    c, ch, gm, x, target, cp = build_workload(device)
+    mode = ndg.NDG_MODE_TC if form == "tc" else ndg.NDG_MODE_FP32
+    tr = Trainer(gm, x, target, TILE, cp, lr=1e-3, t=0.01, phase=0, mode=mode)
+    names = ["build_cull", "forward", "loss", "backward", "adam", "densify"]
+
+    def one_step(traces):
+        tr.set_traces(traces)
+        tr.step(refine=False)
+        tr.refine(sync=False)
+
+    for _ in range(warmup):
+        one_step(None)
+    torch.cuda.synchronize()
+    tr.check()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    traces = [{n: ndg.Trace() for n in names} for _ in range(steps)]
+    pairs = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for i in range(steps):
+            flush.zero_()
+            starts[i].record()
+            one_step(traces[i])
+            ends[i].record()
+            torch.cuda.synchronize()
+            pairs.append(pairs_of(tr.ev.cull, Q, TILE))  # counted outside the timed region
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    st = tr.check()
+    assert st == ndg.NDG_OK, ndg.status_string(st)
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if world > 1:
+        t = torch.tensor([total_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    kern = {n: statistics.mean(tr_[n].ms() for tr_ in traces) for n in names}
+    launches = sum(tr_[n].launches for tr_ in traces for n in names)
+    res = {"value": sum(pairs) * world / (total_ms / 1e3), "ms_per_step": total_ms / steps,
+           "pairs_per_step": statistics.mean(pairs), "candidates_per_step": int(tr.ev.cull.E()),
+           "kernels_ms": kern, "gpu_launches": launches, "clocks": clk.summary()}
+    if e2e_steps:
+        xh = x.cpu().pin_memory()
+        th = target.cpu().pin_memory()
+        e2e_ms = []
+        for i in range(e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            loss = tr.step(xh, th, refine=False)
+            tr.refine(sync=False)
+            float(loss.item())
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        res["e2e"] = {"value": res["pairs_per_step"] / (statistics.mean(e2e_ms[1:]) / 1e3) * world,
+                      "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * 4 + th.numel() * 4),
+                      "d2h_bytes_per_step": 8}
+    res["_c"], res["_ch"] = c, ch
+    del tr, gm, x, target
+    torch.cuda.empty_cache()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -274,6 +351,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-render", action="store_true", help="skip the N=10 1080p render metric")
+    ap.add_argument("--no-fp32-form", action="store_true",
+                    help="skip timing the plain FP32 form next to the chosen form")
     ap.add_argument("--workload", default="fit_n6", choices=sorted(WORKLOADS),
                     help="fit_n6: the headline workload; small_n6: 1/8 of it for profiling")
     args = ap.parse_args()
@@ -291,99 +370,50 @@ def main():
     device = f"cuda:{local}"
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device(device))
-    from paper_2405_20067_gb300 import build, ndg
-    from paper_2405_20067_gb300.train import Trainer
+    from paper_2405_20067_gb300 import build
     build.build()
     peaks, peak_kind = load_peaks()
-    c, ch, gm, x, target, cp = build_workload(device)
-    tr = Trainer(gm, x, target, TILE, cp, lr=1e-3, t=0.01, phase=0)
-    names = ["build_cull", "forward", "loss", "backward", "adam", "densify"]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)  # > 129 MB L2
-
-    def one_step(traces):
-        tr.set_traces(traces)
-        tr.step(refine=False)
-        tr.refine(sync=False)
-
-    for _ in range(args.warmup):
-        one_step(None)
-    torch.cuda.synchronize()
-    tr.check()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    traces = [{n: ndg.Trace() for n in names} for _ in range(args.steps)]
-    pairs = []
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            flush.zero_()
-            starts[i].record()
-            one_step(traces[i])
-            ends[i].record()
-            pairs.append(tr.ev.cull)  # counted after the timed region
-            torch.cuda.synchronize()
-            pairs[-1] = pairs_of(tr.ev.cull, Q, TILE)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    st = tr.check()
-    assert st == ndg.NDG_OK, ndg.status_string(st)
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    total_pairs = sum(pairs) * world
-    value = total_pairs / (total_ms / 1e3)
-    kern = {n: statistics.mean(tr_[n].ms() for tr_ in traces) for n in names}
-    launches = sum(tr_[n].launches for tr_ in traces for n in names)
+    chosen = run_fit("tc", args.steps, args.warmup, device, flush, world,
+                     max(3, args.steps // 2))
+    plain = None
+    if not args.no_fp32_form:
+        plain = run_fit("fp32", max(3, args.steps // 2), 3, device, flush, world, 0)
     fwd_f, bwd_f = flops_per_pair(N_DIM)
-    mean_pairs = statistics.mean(pairs)
-    clocks = clk.summary()
+    mean_pairs = chosen["pairs_per_step"]
+    kern = chosen["kernels_ms"]
     peak_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = fp32_peak_tflops(peak_mhz)
     achieved = mean_pairs * bwd_f / (kern["backward"] / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": "bwd_kernel<6> (per-pair partials)",
+    roofline = {"bound": "alu", "kernel": "bwd_kernel<6> (per-pair partials, FP32 pipe)",
                 "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz "
                                f"(clock from {peak_kind} peaks file)"}
-    kernels = {n: {"ms": round(kern[n], 4)} for n in names}
-    kernels["forward"]["tflops"] = round(mean_pairs * fwd_f / (kern["forward"] / 1e3) / 1e12, 3)
-    kernels["backward"]["tflops"] = round(achieved, 3)
-
-    # end to end through the public API: host inputs copied in, loss read out
-    xh = x.cpu().pin_memory()
-    th = target.cpu().pin_memory()
-    e2e_ms = []
-    for i in range(max(3, args.steps // 2)):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        loss = tr.step(xh, th, refine=False)
-        tr.refine(sync=False)
-        float(loss.item())
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_ms = e2e_ms[1:]
-    e2e = {"value": mean_pairs / (statistics.mean(e2e_ms) / 1e3) * world, "unit": UNIT,
-           "h2d_bytes_per_step": int(xh.numel() * 4 + th.numel() * 4), "d2h_bytes_per_step": 8}
+    kernels = {n: {"ms": round(v, 4)} for n, v in kern.items()}
+    kernels["backward"]["fp32_tflops"] = round(achieved, 3)
+    kernels["forward"]["form"] = "lifted tensor-core (tcgen05 TF32x3)"
     if rank != 0:
         return
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": workload_name(G, Q), "pairs_per_step": mean_pairs,
-                      "candidates_per_step": int(tr.ev.cull.E()),
+    out = {"metric": METRIC, "value": chosen["value"], "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": chosen["ms_per_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": workload_name(G, Q), "form": "tensor-core forward + FP32 backward",
+                      "pairs_per_step": mean_pairs,
+                      "candidates_per_step": chosen["candidates_per_step"],
                       "l2": "256 MB buffer written between timed steps (untimed)",
                       "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
-           "roofline": roofline, "kernels_ms": kernels, "gpu_launches": launches,
-           "e2e": e2e, "clocks": clocks}
+           "roofline": roofline, "kernels_ms": kernels, "gpu_launches": chosen["gpu_launches"],
+           "e2e": chosen["e2e"], "clocks": chosen["clocks"]}
+    if plain is not None:
+        out["fp32_form"] = {"value": plain["value"], "ms_per_step": plain["ms_per_step"],
+                            "forward_ms": round(plain["kernels_ms"]["forward"], 4),
+                            "speedup_of_chosen": round(chosen["value"] / plain["value"], 3)}
     if not args.no_render and args.workload == "fit_n6":
-        out["render"] = render_n10_1080p(device, max(3, args.steps // 2), 3, flush)
+        out["render"] = render_n10_1080p(device, max(3, args.steps // 4), 2, flush)
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(c, ch)
+        out["cpu_baseline"] = cpu_baseline(chosen["_c"], chosen["_ch"])
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()

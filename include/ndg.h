@@ -164,9 +164,12 @@ ndg_status ndg_loss_l2(long long Q, const float* y, const float* target,
  * [Q][3]: writes dl/d(raw parameter) into `grad` (same layout and N, G,
  * has_children as mix; rows >= G untouched).  Recomputes everything from
  * the raw parameters and `cull`; per-Gaussian sums run in a fixed order
- * (no atomics), so results are bit-reproducible.  Requires E < 2^31. */
+ * (no atomics), so results are bit-reproducible.  Requires E < 2^31.
+ * mode NDG_MODE_FP32: centred form on the FP32 pipe; NDG_MODE_TC: the
+ * lifted form on the tensor cores (gradient of the lifted coefficients as
+ * a second GEMM), available for N <= 6 (shared-memory bound). */
 ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q,
-                        const ndg_cull* cull, const float* dy,
+                        const ndg_cull* cull, int mode, const float* dy,
                         ndg_mixture* grad, void* ws, size_t ws_bytes,
                         ndg_stream stream, ndg_trace* trace);
 

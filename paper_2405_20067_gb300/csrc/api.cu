@@ -364,10 +364,11 @@ ndg_status ndg_loss_l2(long long Q, const float* y, const float* target, float* 
 }
 
 ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q, const ndg_cull* cull,
-                        const float* dy, ndg_mixture* grad, void* ws, size_t ws_bytes,
+                        int mode, const float* dy, ndg_mixture* grad, void* ws, size_t ws_bytes,
                         ndg_stream stream, ndg_trace* trace) {
   ndg_status st;
   if ((st = check_mix(mix)) || (st = check_queries(q)) || (st = check_cull(cull))) return st;
+  if (mode != NDG_MODE_FP32 && (mode != NDG_MODE_TC || mix->N > 6)) return NDG_ERR_INVALID_ARG;
   if (!grad || grad->N != mix->N || grad->G != mix->G || grad->has_children != mix->has_children ||
       (st = check_mix(grad)))
     return st ? st : NDG_ERR_INVALID_ARG;
@@ -412,8 +413,9 @@ ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q, const ndg_
   ba.Ge = pa.Ge;
   ba.slot = slot;
   ba.part = (float*)(w + L.part);
+  ba.status = pa.status;
   tr.begin();
-  tr += launch_bwd(N, ba, z.T, s);
+  tr += mode == NDG_MODE_TC ? launch_bwd_tc(N, ba, z.T, s) : launch_bwd(N, ba, z.T, s);
   tr.end();
   float* gsum = (float*)(w + L.gsum);
   tr += launch_segsum(ba.part, part_floats(N), goff, Ge, gsum, s);

@@ -10,7 +10,8 @@
 // and upstream gradients sit in shared memory; each thread keeps its
 // Gaussian's record and its partial sums in registers and loops over the
 // queries (broadcast reads), producing one partial record per candidate
-// entry: sum beta z d^T (lower), sum beta z, sum dy e, beta = e sum_c dy_c w_c.
+// entry: dl/dM = -sum beta z d^T (lower), dl/dm = M^T sum beta z,
+// dl/dw = sum dy e, with beta = e sum_c dy_c w_c.
 // The entries are then transposed to Gaussian-major order by a stable radix
 // sort, summed per Gaussian in entry order (no atomics, bit-reproducible)
 // and chained to the raw parameters (Eq. 2, 6-8) by chain_kernel.
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(LOSS_BLOCKS) loss_final_kernel(const double* _
 // is [sum beta z d^T (lower), sum beta z, sum dy e], formed from
 // sum beta z' (x - c)^T - (sum beta z') (m - c)^T at the end.  Records go to
 // the entry's Gaussian-major slot slot[c], so that the per-Gaussian sums read
-// contiguous memory.
+// contiguous memory.  Record: [dl/dM (lower), dl/dm, dl/dw].
 template <int N>
 __global__ void __launch_bounds__(128) bwd_kernel(BwdArgs a) {
   constexpr int P = tri(N), R = rec_floats(N), R4 = R / 4, RP = part_floats(N);
@@ -304,6 +305,7 @@ __global__ void __launch_bounds__(128) bwd_kernel(BwdArgs a) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       if (cid[h] >= end) continue;
+      // record: dl/dM = -sum beta z d^T (lower), dl/dm = M^T sum beta z, dl/dw
       float buf[RP];
 #pragma unroll
       for (int i = 0; i < N; ++i) {
@@ -311,9 +313,17 @@ __global__ void __launch_bounds__(128) bwd_kernel(BwdArgs a) {
 #pragma unroll
         for (int k = 0; k <= i; ++k) {
           const float gm = h ? GM2[tri(i) + k].y : GM2[tri(i) + k].x;
-          buf[tri(i) + k] = kInvKappa * fmaf(-gz, mt[h][k], gm);
+          buf[tri(i) + k] = -kInvKappa * fmaf(-gz, mt[h][k], gm);
         }
-        buf[P + i] = kInvKappa * gz;
+      }
+      constexpr float kInvKappa2 = kInvKappa * kInvKappa;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        float s = 0.0f;
+#pragma unroll
+        for (int i = k; i < N; ++i) s = fmaf(h ? M2[tri(i) + k].y : M2[tri(i) + k].x,
+                                             h ? Gz2[i].y : Gz2[i].x, s);
+        buf[P + k] = kInvKappa2 * s;
       }
 #pragma unroll
       for (int c = 0; c < 3; ++c) buf[P + N + c] = h ? Gw2[c].y : Gw2[c].x;
@@ -399,35 +409,28 @@ __device__ __forceinline__ void inv_lower(const float* L, float* M) {
   }
 }
 
-// dl/dL (lower) = M^T A M^T where A = sum beta z d^T = -(dl/dM); and
-// dl/dm = M^T sum beta z.
+// dl/dL (lower) = -M^T (dl/dM) M^T for M = L^-1 (dM = -M dL M).
 template <int N>
-__device__ __forceinline__ void grad_L_m(const float* M, const float* A, const float* Gz,
-                                         float* GL, float* Gm) {
-  float H[N][N];  // H = A M^T, H[a][j] = sum_{b <= min(a, j)} A[a][b] M[j][b]
+__device__ __forceinline__ void grad_L(const float* M, const float* GMr, float* GL) {
+  float H[N][N];  // H = GMr M^T, H[a][j] = sum_{b <= min(a, j)} GMr[a][b] M[j][b]
 #pragma unroll
   for (int aa = 0; aa < N; ++aa)
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       float s = 0.0f;
 #pragma unroll
-      for (int b = 0; b <= (aa < j ? aa : j); ++b) s = fmaf(A[tri(aa) + b], M[tri(j) + b], s);
+      for (int b = 0; b <= (aa < j ? aa : j); ++b) s = fmaf(GMr[tri(aa) + b], M[tri(j) + b], s);
       H[aa][j] = s;
     }
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
+  for (int i = 0; i < N; ++i)
 #pragma unroll
     for (int j = 0; j <= i; ++j) {
       float s = 0.0f;
 #pragma unroll
       for (int aa = i; aa < N; ++aa) s = fmaf(M[tri(aa) + i], H[aa][j], s);
-      GL[tri(i) + j] = s;
+      GL[tri(i) + j] = -s;
     }
-    float g = 0.0f;
-#pragma unroll
-    for (int aa = i; aa < N; ++aa) g = fmaf(M[tri(aa) + i], Gz[aa], g);
-    Gm[i] = g;
-  }
 }
 
 template <int N>
@@ -464,7 +467,9 @@ __global__ void __launch_bounds__(128) chain_kernel(ChainArgs a) {
   act_lower32<N>(a.theta + (size_t)g * P, L);
   inv_lower<N>(L, M);
   const float* sp = a.gsum + (size_t)g * RP;
-  grad_L_m<N>(M, sp, sp + P, GL, Gm);
+  grad_L<N>(M, sp, GL);
+#pragma unroll
+  for (int i = 0; i < N; ++i) Gm[i] = sp[P + i];
   if (a.has_children) {
     const float* sc = a.gsum + (size_t)(a.G + g) * RP;
     float U[P], Lc[P], Mc[P], GLc[P], Gmc[N], mu[N];
@@ -481,7 +486,9 @@ __global__ void __launch_bounds__(128) chain_kernel(ChainArgs a) {
       }
     }
     inv_lower<N>(Lc, Mc);
-    grad_L_m<N>(Mc, sc, sc + P, GLc, Gmc);
+    grad_L<N>(Mc, sc, GLc);
+#pragma unroll
+    for (int i = 0; i < N; ++i) Gmc[i] = sc[P + i];
     // L_c = L_p U, m_c = L_p m_u + m_p (Eq. 6-7):
     //   dl/dL_p += lower(GLc U^T) + lower(Gmc m_u^T), dl/dm_p += Gmc,
     //   dl/dU = lower(L_p^T GLc), dl/dm_u = L_p^T Gmc.

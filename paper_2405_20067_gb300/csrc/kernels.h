@@ -55,6 +55,7 @@ struct BwdArgs {
   const int* ids;
   const float* rec;
   int Ge;
+  int* status;               // device status word (timeouts of bounded waits)
   const int32_t* slot;       // entry -> Gaussian-major slot, or null (entry order)
   float* part;               // [E_cap][part_floats(N)]
 };
@@ -107,6 +108,7 @@ int launch_prep(int N, const PrepArgs& a, cudaStream_t s);
 int launch_cull_tile(int KP, const CullTileArgs& a, long long T, cudaStream_t s);
 int launch_fwd(int N, const FwdArgs& a, long long T, cudaStream_t s);
 int launch_fwd_tc(int N, const FwdArgs& a, long long T, cudaStream_t s);
+int launch_bwd_tc(int N, const BwdArgs& a, long long T, cudaStream_t s);  // N <= 6
 size_t fwd_tc_smem(int N);
 int launch_loss(const float* y, const float* target, float* dy, long long n, double* part,
                  double* loss, cudaStream_t s);

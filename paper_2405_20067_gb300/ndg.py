@@ -109,7 +109,7 @@ def lib():
         L.ndg_build_cull.argtypes = [M, Qp, CP, C, _P, sz, _P, TR]
         L.ndg_forward.argtypes = [M, Qp, C, ctypes.c_int, _P, _P, sz, _P, TR]
         L.ndg_loss_l2.argtypes = [ctypes.c_longlong, _P, _P, _P, _P, _P, sz, _P, TR]
-        L.ndg_backward.argtypes = [M, Qp, C, _P, M, _P, sz, _P, TR]
+        L.ndg_backward.argtypes = [M, Qp, C, ctypes.c_int, _P, M, _P, sz, _P, TR]
         L.ndg_adam.argtypes = [M, M, M, M, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                ctypes.c_float, _P, TR]
         L.ndg_densify.argtypes = [M, ctypes.c_float, ctypes.c_float, _P, M, M, _P, _P, sz, _P, TR]
@@ -297,10 +297,11 @@ def loss_l2(y: torch.Tensor, target: torch.Tensor, dy: torch.Tensor, loss: torch
 
 
 def backward(mix: Mixture, x: torch.Tensor, tile: int, cull: Cull, dy: torch.Tensor,
-             grad: Mixture, ws: torch.Tensor, stream=None, trace: Trace | None = None):
+             grad: Mixture, ws: torch.Tensor, mode: int = NDG_MODE_FP32, stream=None,
+             trace: Trace | None = None):
     _check(lib().ndg_backward(ctypes.byref(mix.c()), ctypes.byref(queries_c(x, tile)),
-                              ctypes.byref(cull.c()), _ptr(dy), ctypes.byref(grad.c()), _ptr(ws),
-                              ws.numel(), _stream(stream), _tr(trace)), "ndg_backward")
+                              ctypes.byref(cull.c()), mode, _ptr(dy), ctypes.byref(grad.c()),
+                              _ptr(ws), ws.numel(), _stream(stream), _tr(trace)), "ndg_backward")
 
 
 def adam(params: Mixture, grad: Mixture, m1: Mixture, m2: Mixture, step: torch.Tensor, lr: float,
@@ -379,8 +380,9 @@ class Evaluator:
         forward(mix, self.x, self.tile, self.cull, y, self.ws, mode=mode)
         return y
 
-    def backward(self, mix: Mixture, dy: torch.Tensor, grad: Mixture | None = None) -> Mixture:
+    def backward(self, mix: Mixture, dy: torch.Tensor, grad: Mixture | None = None,
+                 mode: int = NDG_MODE_FP32) -> Mixture:
         if grad is None:
             grad = mix.zeros_like()
-        backward(mix, self.x, self.tile, self.cull, dy, grad, self.ws)
+        backward(mix, self.x, self.tile, self.cull, dy, grad, self.ws, mode=mode)
         return grad

@@ -24,7 +24,8 @@ class NDGEval(torch.autograd.Function):
     @staticmethod
     def forward(ctx, ev: ndg.Evaluator, mix: ndg.Mixture, *params):
         y = torch.empty(ev.x.shape[0], 3, dtype=torch.float32, device=ev.x.device)
-        ndg.forward(mix, ev.x, ev.tile, ev.cull, y, ev.ws, trace=getattr(ev, "trace_fwd", None))
+        ndg.forward(mix, ev.x, ev.tile, ev.cull, y, ev.ws, mode=getattr(ev, "mode", ndg.NDG_MODE_FP32),
+                    trace=getattr(ev, "trace_fwd", None))
         ctx.ev, ctx.mix = ev, mix
         return y
 
@@ -36,7 +37,10 @@ class NDGEval(torch.autograd.Function):
         grad = ndg.Mixture(mix.N, mix.G, *[None if getattr(mix, f) is None
                                            else torch.empty_like(getattr(mix, f))
                                            for f in _PARAMS], has_children=mix.has_children)
-        ndg.backward(mix, ev.x, ev.tile, ev.cull, dy.contiguous(), grad, ev.ws,
+        mode = getattr(ev, "mode", ndg.NDG_MODE_FP32)
+        if mode == ndg.NDG_MODE_TC and mix.N > 6:
+            mode = ndg.NDG_MODE_FP32  # the tensor-core backward covers N <= 6
+        ndg.backward(mix, ev.x, ev.tile, ev.cull, dy.contiguous(), grad, ev.ws, mode=mode,
                      trace=getattr(ev, "trace_bwd", None))
         outs = [getattr(grad, f) if (mix.has_children or i < 4) else None
                 for i, f in enumerate(_PARAMS)]
@@ -56,8 +60,10 @@ class Trainer:
 
     def __init__(self, mix: ndg.Mixture, x: torch.Tensor, target: torch.Tensor, tile: int,
                  cp: ndg.CullParams, lr: float = 1e-3, t: float = 0.01, phase: int = 300,
-                 E_cap: int | None = None, seed: int = 0):
-        self.mix, self.tile, self.cp = mix, tile, cp
+                 E_cap: int | None = None, seed: int = 0, mode: int = ndg.NDG_MODE_FP32):
+        """mode: NDG_MODE_FP32 or NDG_MODE_TC (lifted tensor-core forward, and
+        backward for N <= 6)."""
+        self.mix, self.tile, self.cp, self.mode = mix, tile, cp, mode
         self.lr, self.t, self.phase = lr, t, phase
         for f in _PARAMS:
             p = getattr(mix, f)
@@ -90,6 +96,7 @@ class Trainer:
         """traces: dict name -> ndg.Trace for build_cull / forward / loss /
         backward / adam / densify, or None."""
         self.traces = traces
+        self.ev.mode = self.mode
         self.ev.trace_fwd = traces.get("forward") if traces else None
         self.ev.trace_bwd = traces.get("backward") if traces else None
 
@@ -105,6 +112,7 @@ class Trainer:
         if target is not None:
             self.target.copy_(target, non_blocking=True)
         mix = self.mix
+        self.ev.mode = self.mode
         ndg.build_cull(mix, self.x, self.tile, self.cp, self.ev.cull, self.ev.ws,
                        trace=self._tr("build_cull"))
         with torch.enable_grad():
