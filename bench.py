@@ -271,7 +271,8 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def run_fit(form: str, steps: int, warmup: int, device: str, flush, world: int, e2e_steps: int):
+def run_fit(form: str, steps: int, warmup: int, device: str, flush, world: int, e2e_steps: int,
+            bwd_form: str | None = None):
     """Times `steps` fit steps of the workload in one form ("tc": lifted
     tensor-core forward; "fp32": plain FP32 forward); backward, cull, loss,
     Adam and the refinement check are shared."""
@@ -281,7 +282,8 @@ def run_fit(form: str, steps: int, warmup: int, device: str, flush, world: int, 
     import torch.distributed as dist
     c, ch, gm, x, target, cp = build_workload(device)
     mode = ndg.NDG_MODE_TC if form == "tc" else ndg.NDG_MODE_FP32
-    tr = Trainer(gm, x, target, TILE, cp, lr=1e-3, t=0.01, phase=0, mode=mode)
+    bmode = ndg.NDG_MODE_TC if (bwd_form or form) == "tc" else ndg.NDG_MODE_FP32
+    tr = Trainer(gm, x, target, TILE, cp, lr=1e-3, t=0.01, phase=0, mode=mode, bwd_mode=bmode)
     names = ["build_cull", "forward", "loss", "backward", "adam", "densify"]
 
     def one_step(traces):
@@ -353,6 +355,8 @@ def main():
     ap.add_argument("--no-render", action="store_true", help="skip the N=10 1080p render metric")
     ap.add_argument("--no-fp32-form", action="store_true",
                     help="skip timing the plain FP32 form next to the chosen form")
+    ap.add_argument("--bwd-form", default="fp32", choices=["fp32", "tc"],
+                    help="backward of the chosen form (its forward is the tensor-core one)")
     ap.add_argument("--workload", default="fit_n6", choices=sorted(WORKLOADS),
                     help="fit_n6: the headline workload; small_n6: 1/8 of it for profiling")
     args = ap.parse_args()
@@ -375,7 +379,7 @@ def main():
     peaks, peak_kind = load_peaks()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)  # > 129 MB L2
     chosen = run_fit("tc", args.steps, args.warmup, device, flush, world,
-                     max(3, args.steps // 2))
+                     max(3, args.steps // 2), bwd_form=args.bwd_form)
     plain = None
     if not args.no_fp32_form:
         plain = run_fit("fp32", max(3, args.steps // 2), 3, device, flush, world, 0)
@@ -385,7 +389,8 @@ def main():
     peak_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = fp32_peak_tflops(peak_mhz)
     achieved = mean_pairs * bwd_f / (kern["backward"] / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": "bwd_kernel<6> (per-pair partials, FP32 pipe)",
+    roofline = {"bound": "alu", "kernel": ("bwd_tc_kernel<6>" if args.bwd_form == "tc" else
+                                           "bwd_kernel<6> (per-pair partials, FP32 pipe)"),
                 "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz "
@@ -399,7 +404,8 @@ def main():
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": chosen["ms_per_step"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic",
-           "config": {"workload": workload_name(G, Q), "form": "tensor-core forward + FP32 backward",
+           "config": {"workload": workload_name(G, Q),
+                      "form": f"tensor-core forward + {args.bwd_form} backward",
                       "pairs_per_step": mean_pairs,
                       "candidates_per_step": chosen["candidates_per_step"],
                       "l2": "256 MB buffer written between timed steps (untimed)",

@@ -47,7 +47,8 @@ struct CommonLayout {
   size_t header, rec, loss, dflag, drank, dfresh, end;
 };
 struct CullLayout {
-  size_t tb, range, tkey, gkey, bin, bk_a, bv_a, bk_b, bv_b, binoff, counts, excl, tmp, end;
+  size_t tb, range, tkey, gkey, gkey_sorted, bin, bk_a, bv_a, bk_b, bv_b, binoff, counts, excl, tmp,
+      end;
 };
 struct BwdLayout {
   size_t part, sk_a, sv_a, sk_b, sv_b, goff, gsum, tmp, end;
@@ -75,15 +76,17 @@ CullLayout cull_layout(const Sizes& z, size_t base) {
   c.range = r.take(3 * NDG_MAX_K * sizeof(float));
   c.tkey = r.take((size_t)z.T * 2 * z.KP);
   c.gkey = r.take((size_t)z.Ge_cap * 2 * z.KP);
+  c.gkey_sorted = r.take((size_t)z.Ge_cap * 2 * z.KP);
   c.bin = r.take((size_t)z.Ge_cap * 4);
   c.bk_a = r.take((size_t)z.Ge_cap * 4);
   c.bv_a = r.take((size_t)z.Ge_cap * 4);
   c.bk_b = r.take((size_t)z.Ge_cap * 4);
   c.bv_b = r.take((size_t)z.Ge_cap * 4);
   c.binoff = r.take(((size_t)nb * nb + 1) * sizeof(long long));
-  c.counts = r.take((size_t)(z.T + 1) * sizeof(long long));
-  c.excl = r.take((size_t)(z.T + 1) * sizeof(long long));
-  size_t t1 = radix_temp_bytes(z.Ge_cap), t2 = scan_temp_bytes(z.T + 1);
+  // per (tile, warp slice) survivor counts and their exclusive scan
+  c.counts = r.take((size_t)(8 * z.T + 1) * sizeof(long long));
+  c.excl = r.take((size_t)(8 * z.T + 1) * sizeof(long long));
+  size_t t1 = radix_temp_bytes(z.Ge_cap), t2 = scan_temp_bytes(8 * z.T + 1);
   c.tmp = r.take(t1 > t2 ? t1 : t2);
   c.end = r.off;
   return c;
@@ -176,7 +179,7 @@ __global__ void finalize_offsets_kernel(const long long* __restrict__ excl, long
                                         long long* __restrict__ E_dev, int* status) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t > T) return;
-  long long v = excl[t];
+  long long v = excl[8 * t];  // scanned per (tile, warp slice) counts
   offsets[t] = v < E_cap ? v : E_cap;
   if (t == T) {
     *E_dev = v;
@@ -287,9 +290,11 @@ ndg_status ndg_build_cull(const ndg_mixture* mix, const ndg_queries* q, const nd
                    nullptr, bits_for((long long)nb * nb + 1), w + L.tmp, s, &sk, &sv);
   long long* binoff = (long long*)(w + L.binoff);
   tr += bin_boundaries(sk, pa.Ge, nullptr, nb * nb, binoff, s);
+  uint8_t* gkey_sorted = (uint8_t*)(w + L.gkey_sorted);
+  tr += launch_permute_keys(gkey, sv, pa.Ge, KP, gkey_sorted, s);
   CullTileArgs ca{};
   ca.tkey = tkey;
-  ca.gkey = gkey;
+  ca.gkey = gkey_sorted;
   ca.binoff = binoff;
   ca.sorted_ids = sv;
   ca.B = B;
@@ -299,7 +304,7 @@ ndg_status ndg_build_cull(const ndg_mixture* mix, const ndg_queries* q, const nd
   ca.E_cap = out->E_cap;
   tr += launch_cull_tile(KP, ca, T, s);
   long long* excl = (long long*)(w + L.excl);
-  tr += scan_exclusive_i64(ca.counts, excl, T, w + L.tmp, s);
+  tr += scan_exclusive_i64(ca.counts, excl, 8 * T, w + L.tmp, s);
   finalize_offsets_kernel<<<(unsigned)ceil_div<long long>(T + 1, 256), 256, 0, s>>>(
       excl, T, out->E_cap, out->offsets, out->E_dev, status);
   tr += 1;

@@ -295,13 +295,20 @@ __device__ __forceinline__ bool keys_overlap(const uint32_t* glo, const uint32_t
   return ok == 0xffffffffu;
 }
 
+// One CTA of CT_WARPS warps per tile.  The tile's sources (Gaussians whose
+// first-projection bucket range meets the tile's) are thi0 + 1 runs of the
+// bin-sorted order; warp w takes the contiguous slice w of their
+// concatenation, walks it 32 elements at a time (each lane tracks its run),
+// tests the remaining projections and counts (count pass) or writes (fill
+// pass, at the scanned offset of (tile, warp)) the survivors in order, so the
+// list order is the concatenation order.
 template <int KP>
 __global__ void __launch_bounds__(256) cull_tile_kernel(CullTileArgs a) {
   constexpr int W = KP / 4;  // 32-bit words per key half (KP >= 8)
   __shared__ long long rbeg[256];
   __shared__ long long rpre[257];
-  __shared__ int wcount[8];
   __shared__ long long s_total;
+  __shared__ long long ws_[8];
   const long long t = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t tlo[W > 0 ? W : 1], thi[W > 0 ? W : 1];
@@ -315,48 +322,56 @@ __global__ void __launch_bounds__(256) cull_tile_kernel(CullTileArgs a) {
   }
   const int nb = KP > 0 ? a.B : 1;
   const int nr = thi0 + 1;  // first-projection bucket rows b = 0 .. thi0
-  long long len = 0;
-  if (tid < nr) {
-    long long b0 = a.binoff[(long long)tid * nb + tlo0];
-    long long b1 = a.binoff[(long long)(tid + 1) * nb];
-    rbeg[tid] = b0;
-    len = b1 > b0 ? b1 - b0 : 0;
-  }
-  // exclusive scan of the run lengths (nr <= 256)
   {
+    long long len = 0;
+    if (tid < nr) {
+      long long b0 = a.binoff[(long long)tid * nb + tlo0];
+      long long b1 = a.binoff[(long long)(tid + 1) * nb];
+      rbeg[tid] = b0;
+      len = b1 > b0 ? b1 - b0 : 0;
+    }
     long long v = tid < nr ? len : 0, incl = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       long long u = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += u;
     }
-    __shared__ long long ws_[8];
     if (lane == 31) ws_[warp] = incl;
     __syncthreads();
     long long off = 0;
     for (int w = 0; w < warp; ++w) off += ws_[w];
     if (tid < nr) rpre[tid] = incl - v + off;
-    if (tid == 255) rpre[nr] = incl + off;  // total (all threads past nr add 0)
+    if (tid == 255) rpre[nr] = incl + off;  // total (threads past nr add 0)
     __syncthreads();
     if (tid == 0) s_total = rpre[nr];
     __syncthreads();
   }
   const long long n_src = s_total;
-  const long long base = a.ids ? a.excl[t] : 0;
-  long long written = 0;
-  for (long long i0 = 0; i0 < n_src; i0 += 256) {
-    const long long i = i0 + tid;
+  const long long lo = n_src * warp / 8, hi = n_src * (warp + 1) / 8;
+  // run of the slice's first element: largest r with rpre[r] <= lo
+  int r = 0;
+  {
+    int a0 = 0, b0 = nr - 1;
+    while (a0 < b0) {
+      int mid = (a0 + b0 + 1) >> 1;
+      if (rpre[mid] <= lo) a0 = mid; else b0 = mid - 1;
+    }
+    r = a0;
+  }
+  const bool fill = a.ids != nullptr;
+  long long written = fill ? a.excl[t * 8 + warp] : 0;
+  long long count = 0;
+  for (long long i0 = lo; i0 < hi; i0 += 32) {
+    const long long i = i0 + lane;
     bool pass = false;
     int e = 0;
-    if (i < n_src) {
-      int lo = 0, hi = nr - 1;  // largest r with rpre[r] <= i
-      while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (rpre[mid] <= i) lo = mid; else hi = mid - 1;
-      }
-      e = a.sorted_ids[rbeg[lo] + (i - rpre[lo])];
+    if (i < hi) {
+      while (r + 1 < nr && rpre[r + 1] <= i) ++r;
+      const long long pos = rbeg[r] + (i - rpre[r]);
+      e = a.sorted_ids[pos];
       if (KP > 0) {
-        const uint32_t* gk = reinterpret_cast<const uint32_t*>(a.gkey + (size_t)e * 2 * KP);
+        // keys in bin-sorted order: a warp reads consecutive rows
+        const uint32_t* gk = reinterpret_cast<const uint32_t*>(a.gkey + (size_t)pos * 2 * KP);
         uint32_t glo[W > 0 ? W : 1], ghi[W > 0 ? W : 1];
 #pragma unroll
         for (int w = 0; w < W; ++w) { glo[w] = gk[w]; ghi[w] = gk[W + w]; }
@@ -366,22 +381,23 @@ __global__ void __launch_bounds__(256) cull_tile_kernel(CullTileArgs a) {
       }
     }
     const unsigned bal = __ballot_sync(0xffffffffu, pass);
-    if (lane == 0) wcount[warp] = __popc(bal);
-    __syncthreads();
-    long long before = 0, chunk = 0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) {
-      before += w < warp ? wcount[w] : 0;
-      chunk += wcount[w];
-    }
-    if (a.ids && pass) {
-      long long pos = base + written + before + __popc(bal & ((1u << lane) - 1u));
+    if (fill && pass) {
+      const long long pos = written + count + __popc(bal & ((1u << lane) - 1u));
       if (pos < a.E_cap) a.ids[pos] = e;
     }
-    written += chunk;
-    __syncthreads();
+    count += __popc(bal);
   }
-  if (!a.ids && tid == 0) a.counts[t] = written;
+  if (!fill && lane == 0) a.counts[t * 8 + warp] = count;
+}
+
+// Key rows in bin-sorted order: dst[p] = src[sorted[p]] (2 KP bytes a row).
+__global__ void permute_keys_kernel(const uint8_t* __restrict__ src, const int32_t* __restrict__ sorted,
+                                    int n, int row_words, uint32_t* __restrict__ dst) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)n * row_words) return;
+  const long long p = i / row_words;
+  const int w = (int)(i - p * row_words);
+  dst[i] = reinterpret_cast<const uint32_t*>(src + (size_t)sorted[p] * row_words * 4)[w];
 }
 
 // ---- launchers ------------------------------------------------------------------
@@ -425,6 +441,15 @@ int launch_prep(int N, const PrepArgs& a, cudaStream_t s) {
 #define L_PREP(n) prep_kernel<n><<<blocks, 128, 0, s>>>(a)
   NDG_SWITCH_N(N, L_PREP)
 #undef L_PREP
+  return 1;
+}
+
+int launch_permute_keys(const uint8_t* src, const int32_t* sorted, int n, int KP, uint8_t* dst,
+                        cudaStream_t s) {
+  if (n <= 0 || KP <= 0) return 0;
+  const int row_words = 2 * KP / 4;
+  permute_keys_kernel<<<(unsigned)ceil_div<long long>((long long)n * row_words, 256), 256, 0, s>>>(
+      src, sorted, n, row_words, reinterpret_cast<uint32_t*>(dst));
   return 1;
 }
 

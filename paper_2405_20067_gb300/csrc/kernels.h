@@ -24,11 +24,11 @@ struct PrepArgs {
 
 struct CullTileArgs {
   const uint8_t* tkey;        // [T][2 KP]
-  const uint8_t* gkey;        // [Ge][2 KP]
+  const uint8_t* gkey;        // [Ge][2 KP] in bin-sorted order (row p for sorted_ids[p])
   const long long* binoff;    // [nb * nb + 1]
   const int32_t* sorted_ids;  // Gaussians sorted by bin
   int B;
-  long long* counts;          // count pass: [T]
+  long long* counts;          // count pass: [T][8] per warp slice
   const long long* excl;      // fill pass: exclusive scan of counts
   int* ids;                   // fill pass: [E_cap]
   long long E_cap;
@@ -106,6 +106,8 @@ int launch_tile_keys(const float* tb, long long T, int k, int KP, int B, const f
                       uint8_t* tkey, cudaStream_t s);
 int launch_prep(int N, const PrepArgs& a, cudaStream_t s);
 int launch_cull_tile(int KP, const CullTileArgs& a, long long T, cudaStream_t s);
+int launch_permute_keys(const uint8_t* src, const int32_t* sorted, int n, int KP, uint8_t* dst,
+                        cudaStream_t s);
 int launch_fwd(int N, const FwdArgs& a, long long T, cudaStream_t s);
 int launch_fwd_tc(int N, const FwdArgs& a, long long T, cudaStream_t s);
 int launch_bwd_tc(int N, const BwdArgs& a, long long T, cudaStream_t s);  // N <= 6

@@ -104,9 +104,17 @@ int scan_exclusive_i64(const long long* in, long long* out, long long n, void* t
 }
 
 // ---- stable LSD radix sort, 8 bits per pass -------------------------------
+// Tiles of RS_TILE keys per block; inside a block each warp owns a contiguous
+// run of 32 * RS_ITEMS keys (lane l holds keys j * 32 + l).  Ranks keep the
+// input order among equal digits: warp-level multisplit (match_any) in the
+// order (j, lane) with warp-private digit histograms, an exclusive prefix over
+// the warps of the block, then the block's global digit offsets from the scan
+// of all (digit, block) counts.  Keys are reordered in shared memory first so
+// that every digit's run is written to global memory contiguously.
 constexpr int RS_THREADS = 256;
-constexpr int RS_ROUNDS = 16;
-constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ITEMS = 8;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 
 __device__ __forceinline__ long long rs_count(long long n_cap, const long long* n_dev) {
   if (!n_dev) return n_cap;
@@ -114,62 +122,110 @@ __device__ __forceinline__ long long rs_count(long long n_cap, const long long* 
   return n < n_cap ? (n < 0 ? 0 : n) : n_cap;
 }
 
-__global__ void __launch_bounds__(RS_THREADS) rs_hist(const uint32_t* keys, long long n_cap,
-                                                      const long long* n_dev, int shift,
-                                                      long long* counts, int nblocks) {
+__global__ void __launch_bounds__(RS_THREADS) rs_hist(const uint32_t* __restrict__ keys,
+                                                      long long n_cap, const long long* n_dev,
+                                                      int shift, long long* __restrict__ counts,
+                                                      int nblocks) {
   __shared__ int h[256];
   h[threadIdx.x] = 0;
   __syncthreads();
   const long long n = rs_count(n_cap, n_dev);
   const long long base = (long long)blockIdx.x * RS_TILE;
-  for (int r = 0; r < RS_ROUNDS; ++r) {
-    long long i = base + r * RS_THREADS + threadIdx.x;
-    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < RS_ITEMS; ++j) {
+    const long long i = base + (long long)warp * 32 * RS_ITEMS + j * 32 + lane;
+    const bool valid = i < n;
+    const int d = valid ? (int)((keys[i] >> shift) & 255u) : 256 + lane;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    if (valid && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&h[d], __popc(peers));
   }
   __syncthreads();
   counts[(long long)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-// Scatter with ranks that keep the input order among equal digits: elements
-// are taken in rounds of 256 in index order; inside a round the rank of an
-// element is (earlier rounds) + (lower warps of this round) + (lower lanes).
-__global__ void __launch_bounds__(RS_THREADS) rs_scatter(const uint32_t* kin, const int32_t* vin,
-                                                         uint32_t* kout, int32_t* vout,
+__global__ void __launch_bounds__(RS_THREADS) rs_scatter(const uint32_t* __restrict__ kin,
+                                                         const int32_t* __restrict__ vin,
+                                                         uint32_t* __restrict__ kout,
+                                                         int32_t* __restrict__ vout,
                                                          long long n_cap, const long long* n_dev,
-                                                         int shift, const long long* offs,
+                                                         int shift, const long long* __restrict__ offs,
                                                          int nblocks) {
-  constexpr int NW = RS_THREADS / 32;
-  __shared__ long long run[256];
-  __shared__ int wc[NW][256];
+  __shared__ int wh[RS_WARPS][256];   // per-warp digit counts, then per-warp exclusive prefix
+  __shared__ int bstart[257];         // block-local start of each digit
+  __shared__ long long goff[256];     // global offset of each digit for this block
+  __shared__ uint32_t sk[RS_TILE];
+  __shared__ int32_t sv[RS_TILE];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  run[tid] = offs[(long long)tid * nblocks + blockIdx.x];
   const long long n = rs_count(n_cap, n_dev);
   const long long base = (long long)blockIdx.x * RS_TILE;
-  const unsigned lt_mask = (1u << lane) - 1u;
-  for (int r = 0; r < RS_ROUNDS; ++r) {
 #pragma unroll
-    for (int w = 0; w < NW; ++w) wc[w][tid] = 0;
-    __syncthreads();
-    long long i = base + r * RS_THREADS + tid;
-    bool valid = i < n;
-    uint32_t key = valid ? kin[i] : 0u;
-    int d = valid ? (int)((key >> shift) & 255u) : 256 + lane;  // invalid lanes match nobody
-    unsigned peers = __match_any_sync(0xffffffffu, d);
-    int wrank = __popc(peers & lt_mask);
-    if (valid && wrank == 0) wc[warp][d] = __popc(peers);
-    __syncthreads();
-    if (valid) {
-      long long pos = run[d] + wrank;
-      for (int w = 0; w < warp; ++w) pos += wc[w][d];
-      kout[pos] = key;
-      vout[pos] = vin ? vin[i] : (int32_t)i;
+  for (int w = 0; w < RS_WARPS; ++w) wh[w][tid] = 0;
+  goff[tid] = offs[(long long)tid * nblocks + blockIdx.x];
+  __syncthreads();
+  uint32_t key[RS_ITEMS];
+  int32_t val[RS_ITEMS];
+  int dig[RS_ITEMS], rank[RS_ITEMS];
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int j = 0; j < RS_ITEMS; ++j) {
+    const long long i = base + (long long)warp * 32 * RS_ITEMS + j * 32 + lane;
+    const bool valid = i < n;
+    key[j] = valid ? kin[i] : 0u;
+    val[j] = valid ? (vin ? vin[i] : (int32_t)i) : 0;
+    const int d = valid ? (int)((key[j] >> shift) & 255u) : 256 + lane;
+    dig[j] = d;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    int before = 0;
+    if (valid) before = wh[warp][d];
+    __syncwarp();
+    rank[j] = before + __popc(peers & lt);
+    if (valid && (peers & lt) == 0) wh[warp][d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // exclusive prefix over warps (per digit) and block-local digit starts
+  {
+    int run = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) {
+      const int c = wh[w][tid];
+      wh[w][tid] = run;
+      run += c;
     }
-    __syncthreads();
-    int add = 0;
+    // run = block total of digit tid; exclusive scan over digits
+    int incl = run;
 #pragma unroll
-    for (int w = 0; w < NW; ++w) add += wc[w][tid];
-    run[tid] += add;
+    for (int o = 1; o < 32; o <<= 1) {
+      int u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    __shared__ int wsum[RS_WARPS];
+    if (lane == 31) wsum[warp] = incl;
     __syncthreads();
+    int off = 0;
+    for (int w = 0; w < warp; ++w) off += wsum[w];
+    bstart[tid] = incl - run + off;
+    if (tid == RS_THREADS - 1) bstart[256] = incl + off;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < RS_ITEMS; ++j) {
+    const int d = dig[j];
+    if (d < 256) {
+      const int p = bstart[d] + wh[warp][d] + rank[j];
+      sk[p] = key[j];
+      sv[p] = val[j];
+    }
+  }
+  __syncthreads();
+  const int nvalid = bstart[256];
+  for (int p = tid; p < nvalid; p += RS_THREADS) {
+    const uint32_t k = sk[p];
+    const int d = (int)((k >> shift) & 255u);
+    const long long g = goff[d] + (p - bstart[d]);
+    kout[g] = k;
+    vout[g] = sv[p];
   }
 }
 

@@ -77,6 +77,36 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// 16-byte asynchronous copy global -> shared (L2 only), and an arrive on
+// `bar` once all of this thread's earlier cp.async copies have landed (the
+// barrier's expected count includes this arrival).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// Bounded wait that gives up early once another thread has raised *abort.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, uint32_t limit,
+                                                   volatile int* abort) {
+  for (uint32_t i = 0; i < limit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 1023u) == 1023u && *abort) return false;
+  }
+  return false;
+}
+
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
                                          uint32_t idesc, uint32_t accumulate) {
   asm volatile(
@@ -107,6 +137,24 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// x32 load without the wait (several may be in flight; tmem_wait_ld() ends them).
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
@@ -181,25 +229,94 @@ struct TcShape {
   static constexpr uint32_t SBO_B = (KP / 4) * 128;
   static constexpr uint32_t A_BYTES = 128u * KP * 4;
   static constexpr uint32_t B_BYTES = (uint32_t)NC * KP * 4;
-  static constexpr uint32_t SMEM_USED = 2 * A_BYTES + 2 * B_BYTES + NC * 16 + 128;
-  // at most 512 / NC CTAs may share an SM's tensor memory: request enough
-  // shared memory that no more than that many are resident
-  static constexpr uint32_t SMEM_FLOOR = (228u * 1024u) / (512u / NC + 1) + 1024u;
+  static constexpr uint32_t W_BYTES = (uint32_t)NC * 16;  // pairs: w0 w0' w1 w1' w2 w2' - -
+  static constexpr uint32_t TMEM_COLS = 2 * NC;          // two accumulators
+  static constexpr uint32_t SMEM_USED = 2 * A_BYTES + 2 * (2 * B_BYTES + W_BYTES) + 128;
+  // at most 512 / TMEM_COLS CTAs may share an SM's tensor memory: request
+  // enough shared memory that no more than that many are resident
+  static constexpr uint32_t SMEM_FLOOR = (228u * 1024u) / (512u / TMEM_COLS + 1) + 1024u;
   static constexpr uint32_t SMEM = SMEM_USED > SMEM_FLOOR ? SMEM_USED : SMEM_FLOOR;
+  static_assert(SMEM <= 227u * 1024u, "shared memory");
 };
+
+// Loads the prepared record of candidate j of a chunk (zeros past the end or
+// for an index outside the mixture).
+template <int N>
+__device__ __forceinline__ void load_record(const FwdArgs& a, long long c0, int n, int j,
+                                            float4 (&rec)[rec_floats(N) / 4]) {
+  constexpr int R4 = rec_floats(N) / 4;
+  const int g = j < n ? a.ids[c0 + j] : -1;
+  if ((unsigned)g < (unsigned)a.Ge) {
+    const float4* src = reinterpret_cast<const float4*>(a.rec) + (size_t)g * R4;
+#pragma unroll
+    for (int i = 0; i < R4; ++i) rec[i] = __ldg(src + i);
+  } else {
+#pragma unroll
+    for (int i = 0; i < R4; ++i) rec[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// Stages candidate j from its record (A packed, m, w; all zero for a
+// padding slot): coefficient row (split hi / lo) into the Coef buffers and
+// its weights into the packed pair array.
+template <int N>
+__device__ __forceinline__ void stage_coef(const float4 (&rec)[rec_floats(N) / 4], int j,
+                                           const float* __restrict__ sctr, uint8_t* Bhi,
+                                           uint8_t* Blo, float* sw2) {
+  using S = TcShape<N>;
+  constexpr int P = S::P, KP = S::KP, R = rec_floats(N), R4 = R / 4;
+  float buf[R];
+#pragma unroll
+  for (int i = 0; i < R4; ++i) {
+    buf[4 * i] = rec[i].x; buf[4 * i + 1] = rec[i].y; buf[4 * i + 2] = rec[i].z; buf[4 * i + 3] = rec[i].w;
+  }
+  const bool live = buf[P + N] != 0.0f || buf[P + N + 1] != 0.0f || buf[P + N + 2] != 0.0f ||
+                    buf[0] != 0.0f;
+  float coef[KP];
+  float mt[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) mt[i] = live ? buf[P + i] - sctr[i] : 0.0f;
+  float cst = 0.0f;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < N; ++k) s = fmaf(buf[i >= k ? tri(i) + k : tri(k) + i], mt[k], s);
+    coef[P + i] = kNegHalfLog2eTC * (-2.0f * s);
+    cst = fmaf(mt[i], s, cst);
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int k = 0; k <= i; ++k)
+      coef[tri(i) + k] = kNegHalfLog2eTC * (i == k ? buf[tri(i) + k] : 2.0f * buf[tri(i) + k]);
+  coef[P + N] = kNegHalfLog2eTC * cst;
+#pragma unroll
+  for (int k = P + N + 1; k < KP; ++k) coef[k] = 0.0f;
+  store_row_split<KP>(Bhi, Blo, j, S::SBO_B, coef);
+  float* d = sw2 + (j >> 1) * 8 + (j & 1);
+  d[0] = buf[P + N];
+  d[2] = buf[P + N + 1];
+  d[4] = buf[P + N + 2];
+}
+
+// As stage_coef, for the warp-specialised kernel's stage layout.
+template <int N>
+__device__ __forceinline__ void stage_coef_ws(const float4 (&rec)[rec_floats(N) / 4], int j,
+                                              const float* __restrict__ sctr, uint8_t* Bhi,
+                                              uint8_t* Blo, float* sw2);
 
 template <int N>
 __global__ void __launch_bounds__(128) fwd_tc_kernel(FwdArgs a) {
   using S = TcShape<N>;
-  constexpr int P = S::P, KP = S::KP, NC = S::NC, R = rec_floats(N), R4 = R / 4;
+  constexpr int P = S::P, KP = S::KP, NC = S::NC;
   extern __shared__ __align__(128) uint8_t dsm[];
   uint8_t* base = (uint8_t*)(((uintptr_t)dsm + 127) & ~(uintptr_t)127);
   uint8_t* Ahi = base;
   uint8_t* Alo = Ahi + S::A_BYTES;
-  uint8_t* Bhi = Alo + S::A_BYTES;
-  uint8_t* Blo = Bhi + S::B_BYTES;
-  float4* sw = reinterpret_cast<float4*>(Blo + S::B_BYTES);
-  __shared__ uint64_t mbar;
+  uint8_t* Bbuf = Alo + S::A_BYTES;  // two stages of (Bhi, Blo, w)
+  constexpr uint32_t STAGE = 2 * S::B_BYTES + S::W_BYTES;
+  __shared__ uint64_t bar[2];
   __shared__ uint32_t tmem_base;
   __shared__ float sred[4 * N * 2];
   __shared__ float sctr[N];
@@ -240,116 +357,110 @@ __global__ void __launch_bounds__(128) fwd_tc_kernel(FwdArgs a) {
     store_row_split<KP>(Ahi, Alo, tid, S::SBO_A, phi);
   }
   if (warp == 0) {
-    tmem_alloc(&tmem_base, NC < 32 ? 32 : NC);
+    tmem_alloc(&tmem_base, S::TMEM_COLS);
     tmem_relinquish();
   }
   if (tid == 0) {
-    mbar_init(&mbar, 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  const long long beg = a.offsets[t], end = a.offsets[t + 1];
+  const int nchunks = (int)((end - beg + NC - 1) / NC);
+  auto chunk_n = [&](int i) -> int {
+    const long long c0 = beg + (long long)i * NC;
+    return (int)(end - c0 < NC ? end - c0 : NC);
+  };
+  // Each thread stages candidates tid (and tid + 128 when NC = 256) of every
+  // chunk; records of the chunk after next are prefetched into registers
+  // during the epilogue, so the gather latency hides behind the MUFU work.
+  static_assert(NC <= 128, "one candidate per thread");
+  float4 pre[rec_floats(N) / 4];
+  if (nchunks > 0) {
+    load_record<N>(a, beg, chunk_n(0), tid, pre);
+    uint8_t* st = Bbuf;
+    if (tid < NC)
+      stage_coef<N>(pre, tid, sctr, st, st + S::B_BYTES,
+                    reinterpret_cast<float*>(st + 2 * S::B_BYTES));
+  }
+  if (nchunks > 1) load_record<N>(a, beg + NC, chunk_n(1), tid, pre);
   fence_proxy_async();
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = tmem_base;
-  const uint32_t my_lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
   constexpr uint32_t IDESC = idesc_tf32(NC);
+  auto issue = [&](int i) {  // MMA of chunk i from stage buffer i & 1 into accumulator i & 1
+    fence_after_sync();
+    uint8_t* st = Bbuf + (i & 1) * STAGE;
+    const uint32_t d = tmem + (uint32_t)((i & 1) * NC);
+    const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo);
+    const uint32_t bh = smem_u32(st), bl = smem_u32(st + S::B_BYTES);
+#pragma unroll
+    for (int ks = 0; ks < KP / 8; ++ks) {
+      const uint32_t ko = (uint32_t)ks * 256u;  // two core matrices per K step of 8
+      const uint64_t dah = smem_desc(ah + ko, 128, S::SBO_A);
+      const uint64_t dal = smem_desc(al + ko, 128, S::SBO_A);
+      const uint64_t dbh = smem_desc(bh + ko, 128, S::SBO_B);
+      const uint64_t dbl = smem_desc(bl + ko, 128, S::SBO_B);
+      mma_tf32(d, dah, dbh, IDESC, ks > 0 ? 1u : 0u);
+      mma_tf32(d, dah, dbl, IDESC, 1u);
+      mma_tf32(d, dal, dbh, IDESC, 1u);
+    }
+    mma_commit(&bar[i & 1]);
+  };
+  if (nchunks > 0 && tid == 0) issue(0);
 
   float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-  const long long beg = a.offsets[t], end = a.offsets[t + 1];
-  uint32_t phase = 0;
-  for (long long c0 = beg; c0 < end; c0 += NC) {
-    const int n = (int)(end - c0 < NC ? end - c0 : NC);
-    // staging: coefficient rows of the chunk's candidates
-    for (int j = tid; j < NC; j += 128) {
-      const int g = j < n ? a.ids[c0 + j] : -1;
-      float coef[KP];
-      float4 wv = make_float4(0.f, 0.f, 0.f, 0.f);
-      if ((unsigned)g < (unsigned)a.Ge) {
-        const float4* src = reinterpret_cast<const float4*>(a.rec) + (size_t)g * R4;
-        float buf[R];
-#pragma unroll
-        for (int i = 0; i < R4; ++i) {
-          float4 v = __ldg(src + i);
-          buf[4 * i] = v.x; buf[4 * i + 1] = v.y; buf[4 * i + 2] = v.z; buf[4 * i + 3] = v.w;
-        }
-        float mt[N], u[N];
-#pragma unroll
-        for (int i = 0; i < N; ++i) mt[i] = buf[P + i] - sctr[i];
-        float cst = 0.0f;
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          float s = 0.0f;
-#pragma unroll
-          for (int k = 0; k < N; ++k) s = fmaf(buf[i >= k ? tri(i) + k : tri(k) + i], mt[k], s);
-          u[i] = s;
-          cst = fmaf(mt[i], s, cst);
-        }
-#pragma unroll
-        for (int i = 0; i < N; ++i)
-#pragma unroll
-          for (int k = 0; k <= i; ++k)
-            coef[tri(i) + k] = kNegHalfLog2eTC * (i == k ? buf[tri(i) + k] : 2.0f * buf[tri(i) + k]);
-#pragma unroll
-        for (int i = 0; i < N; ++i) coef[P + i] = kNegHalfLog2eTC * (-2.0f * u[i]);
-        coef[P + N] = kNegHalfLog2eTC * cst;
-        wv = make_float4(buf[P + N], buf[P + N + 1], buf[P + N + 2], 0.0f);
-      } else {
-#pragma unroll
-        for (int k = 0; k < P + N + 1; ++k) coef[k] = 0.0f;
-      }
-#pragma unroll
-      for (int k = P + N + 1; k < KP; ++k) coef[k] = 0.0f;
-      store_row_split<KP>(Bhi, Blo, j, S::SBO_B, coef);
-      sw[j] = wv;
+  uint32_t phase[2] = {0u, 0u};
+  for (int i = 0; i < nchunks; ++i) {
+    // stage chunk i + 1 while the tensor core works on chunk i; its buffer
+    // was last read by MMA(i - 1), which completed before epilogue(i - 1)
+    if (i + 1 < nchunks && tid < NC) {
+      uint8_t* st = Bbuf + ((i + 1) & 1) * STAGE;
+      stage_coef<N>(pre, tid, sctr, st, st + S::B_BYTES,
+                    reinterpret_cast<float*>(st + 2 * S::B_BYTES));
     }
     fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
-      fence_after_sync();
-      const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
-#pragma unroll
-      for (int ks = 0; ks < KP / 8; ++ks) {
-        const uint32_t ko = (uint32_t)ks * 256u;  // two core matrices per K step of 8
-        const uint64_t dah = smem_desc(ah + ko, 128, S::SBO_A);
-        const uint64_t dal = smem_desc(al + ko, 128, S::SBO_A);
-        const uint64_t dbh = smem_desc(bh + ko, 128, S::SBO_B);
-        const uint64_t dbl = smem_desc(bl + ko, 128, S::SBO_B);
-        mma_tf32(tmem, dah, dbh, IDESC, ks > 0 ? 1u : 0u);
-        mma_tf32(tmem, dah, dbl, IDESC, 1u);
-        mma_tf32(tmem, dal, dbh, IDESC, 1u);
-      }
-      mma_commit(&mbar);
-    }
-    if (!mbar_wait_bounded(&mbar, phase, kWaitLimit)) {
+    fence_before_sync();
+    __syncthreads();  // staging done, epilogue(i - 1) done: accumulator (i + 1) & 1 is free
+    if (i + 1 < nchunks && tid == 0) issue(i + 1);
+    if (i + 2 < nchunks) load_record<N>(a, beg + (long long)(i + 2) * NC, chunk_n(i + 2), tid, pre);
+    if (!mbar_wait_bounded(&bar[i & 1], phase[i & 1], kWaitLimit)) {
       atomicExch(&s_abort, 1);
       if (a.status) set_status(a.status, NDG_ERR_TIMEOUT);
     }
-    phase ^= 1u;
+    phase[i & 1] ^= 1u;
     fence_after_sync();
-    __syncthreads();
+    __syncthreads();  // s_abort is read only right after a barrier: uniform
     if (s_abort) break;
-    // epilogue: row tid of S, NC columns
-#pragma unroll 1
-    for (int cb = 0; cb < NC; cb += 32) {
-      float v[32];
-      tmem_ld32(my_lane_addr + (uint32_t)cb, v);
+    const float* sw2 = reinterpret_cast<const float*>(Bbuf + (i & 1) * STAGE + 2 * S::B_BYTES);
+    const uint32_t acc_addr = tmem + lane_off + (uint32_t)((i & 1) * NC);
+    // all NC columns of this thread's row in flight at once, one wait
+    uint32_t v[NC];
 #pragma unroll
-      for (int j = 0; j < 32; j += 2) {
-        const float2 e = make_float2(ex2_approx(v[j]), ex2_approx(v[j + 1]));
-        const float4 w0 = sw[cb + j], w1 = sw[cb + j + 1];
-        acc[0] = __ffma2_rn(make_float2(w0.x, w1.x), e, acc[0]);
-        acc[1] = __ffma2_rn(make_float2(w0.y, w1.y), e, acc[1]);
-        acc[2] = __ffma2_rn(make_float2(w0.z, w1.z), e, acc[2]);
-      }
+    for (int cb = 0; cb < NC; cb += 32) tmem_ld32_nowait(acc_addr + (uint32_t)cb, v + cb);
+    tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < NC; j += 2) {
+      const float2 e = make_float2(ex2_approx(__uint_as_float(v[j])),
+                                   ex2_approx(__uint_as_float(v[j + 1])));
+      const float4 w01 = *reinterpret_cast<const float4*>(sw2 + (j >> 1) * 8);
+      const float2 w2p = *reinterpret_cast<const float2*>(sw2 + (j >> 1) * 8 + 4);
+      acc[0] = __ffma2_rn(make_float2(w01.x, w01.y), e, acc[0]);
+      acc[1] = __ffma2_rn(make_float2(w01.z, w01.w), e, acc[1]);
+      acc[2] = __ffma2_rn(w2p, e, acc[2]);
     }
     fence_before_sync();
-    __syncthreads();
+    __syncthreads();  // the next iteration restages buffer (i + 2) & 1 = i & 1
   }
+  __syncthreads();
   if (s_abort) {
-    // let any MMA still in flight finish before TMEM is released
-    mbar_wait_bounded(&mbar, phase, kWaitLimit);
+    // let any MMA still in flight finish before tensor memory is released
+    mbar_wait_bounded(&bar[0], phase[0], kWaitLimit);
+    mbar_wait_bounded(&bar[1], phase[1], kWaitLimit);
   }
   if (active && !s_abort) {
 #pragma unroll
@@ -359,7 +470,327 @@ __global__ void __launch_bounds__(128) fwd_tc_kernel(FwdArgs a) {
   __syncthreads();
   if (warp == 0) {
     fence_after_sync();
-    tmem_dealloc(tmem, NC < 32 ? 32 : NC);
+    tmem_dealloc(tmem, S::TMEM_COLS);
+  }
+}
+
+// ---- warp-specialised forward ------------------------------------------------------
+// Same arithmetic as above, organised as a pipeline inside the CTA (one CTA
+// per 128-query block):
+//   warp 8      loader: reads the chunk's candidate indices and gathers their
+//               prepared records into a ring of RS shared-memory stages with
+//               16-byte cp.async copies (completion on rec_full[r]);
+//   warps 0-3   builders: one candidate each; turn a record stage into a
+//               coefficient stage (split TF32 hi/lo, CS stages) and release
+//               the record stage; after a named barrier, thread 0 issues the
+//               chunk's MMAs into one of two TMEM accumulators and commits to
+//               acc_full[b] and coef_empty[s];
+//   warps 4-7   epilogue: one query row each (TMEM lanes 32 (w % 4) + lane);
+//               read the accumulator, release it (acc_empty[b]), then
+//               exp2 + weighted RGB sum with the stage's weights, release the
+//               coefficient stage (coef_empty[s]).
+// Every wait is bounded and gives up once any thread has timed out.
+template <int N>
+struct WsShape {
+  static constexpr int P = tri(N);
+  static constexpr int F = P + N + 1;
+  static constexpr int KP = (F + 7) / 8 * 8;
+  static constexpr int NC = N <= 6 ? 128 : (N <= 10 ? 64 : 32);
+  static constexpr int R = rec_floats(N);
+  static constexpr uint32_t RB = (uint32_t)R * 4;  // bytes per record (multiple of 16)
+  static constexpr int CS = N <= 6 ? 3 : 2;        // coefficient stages
+  static constexpr int RS = N <= 6 ? 4 : (N <= 10 ? 3 : 2);  // record stages
+  static constexpr uint32_t SBO = (KP / 4) * 128;
+  static constexpr uint32_t A_BYTES = 128u * KP * 4;
+  static constexpr uint32_t B_BYTES = (uint32_t)NC * KP * 4;
+  static constexpr uint32_t W_BYTES = (uint32_t)NC * 16;
+  static constexpr uint32_t C_STAGE = 2 * B_BYTES + W_BYTES;
+  static constexpr uint32_t R_STAGE = (uint32_t)NC * RB;
+  static constexpr uint32_t ID_BYTES = (uint32_t)NC * 4;
+  static constexpr uint32_t TMEM_COLS = 2 * NC;
+  static constexpr uint32_t SMEM_USED =
+      2 * A_BYTES + CS * C_STAGE + RS * (R_STAGE + ID_BYTES) + 128;
+  static constexpr uint32_t SMEM_FLOOR = (228u * 1024u) / (512u / TMEM_COLS + 1) + 1024u;
+  static constexpr uint32_t SMEM = SMEM_USED > SMEM_FLOOR ? SMEM_USED : SMEM_FLOOR;
+  static_assert(SMEM <= 227u * 1024u, "shared memory");
+};
+
+template <int N>
+__device__ __forceinline__ void stage_coef_ws(const float4 (&rec)[rec_floats(N) / 4], int j,
+                                              const float* __restrict__ sctr, uint8_t* Bhi,
+                                              uint8_t* Blo, float* sw2) {
+  using S = WsShape<N>;
+  constexpr int P = S::P, KP = S::KP, R = rec_floats(N), R4 = R / 4;
+  float buf[R];
+#pragma unroll
+  for (int i = 0; i < R4; ++i) {
+    buf[4 * i] = rec[i].x; buf[4 * i + 1] = rec[i].y; buf[4 * i + 2] = rec[i].z; buf[4 * i + 3] = rec[i].w;
+  }
+  float coef[KP];
+  float mt[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) mt[i] = buf[P + i] - sctr[i];
+  float cst = 0.0f;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float sacc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < N; ++k) sacc = fmaf(buf[i >= k ? tri(i) + k : tri(k) + i], mt[k], sacc);
+    coef[P + i] = kNegHalfLog2eTC * (-2.0f * sacc);
+    cst = fmaf(mt[i], sacc, cst);
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int k = 0; k <= i; ++k)
+      coef[tri(i) + k] = kNegHalfLog2eTC * (i == k ? buf[tri(i) + k] : 2.0f * buf[tri(i) + k]);
+  coef[P + N] = kNegHalfLog2eTC * cst;
+#pragma unroll
+  for (int k = P + N + 1; k < KP; ++k) coef[k] = 0.0f;
+  store_row_split<KP>(Bhi, Blo, j, S::SBO, coef);
+  float* d = sw2 + (j >> 1) * 8 + (j & 1);
+  d[0] = buf[P + N];
+  d[2] = buf[P + N + 1];
+  d[4] = buf[P + N + 2];
+}
+
+template <int N>
+__global__ void __launch_bounds__(288, 1) fwd_tcws_kernel(FwdArgs a) {
+  using S = WsShape<N>;
+  constexpr int P = S::P, KP = S::KP, NC = S::NC, CS = S::CS, RS = S::RS, R = S::R;
+  extern __shared__ __align__(128) uint8_t dsm[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)dsm + 127) & ~(uintptr_t)127);
+  uint8_t* Ahi = base;
+  uint8_t* Alo = Ahi + S::A_BYTES;
+  uint8_t* Cst = Alo + S::A_BYTES;           // CS stages of (Bhi, Blo, w pairs)
+  uint8_t* Rst = Cst + CS * S::C_STAGE;      // RS stages of records
+  int* Ids = reinterpret_cast<int*>(Rst + RS * S::R_STAGE);  // RS stages of indices
+  __shared__ uint64_t rec_full[RS], rec_empty[RS], coef_empty[CS], acc_full[2], acc_empty[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ float sred[4 * N * 2];
+  __shared__ float sctr[N];
+  __shared__ int s_abort;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int halves = (a.tile + 127) >> 7;
+  const long long t = blockIdx.x / halves;
+  const int half = blockIdx.x - (int)(t * halves);
+  const long long qt = t * a.tile;
+  const long long q0 = qt + half * 128;
+  const long long qend_tile = qt + a.tile < a.Q ? qt + a.tile : a.Q;
+  const int nq = (int)(qend_tile - q0 < 128 ? qend_tile - q0 : 128);
+  const bool is_epi = warp >= 4 && warp < 8;
+  const int qrow = tid - 128;  // epilogue: query row (TMEM lane)
+  const bool active = is_epi && qrow < nq;
+
+  // ---- setup: centre (from the epilogue warps' queries), Phi rows, barriers, TMEM
+  if (tid == 0) {
+    for (int i = 0; i < RS; ++i) { mbar_init(&rec_full[i], 32); mbar_init(&rec_empty[i], 128); }
+    for (int i = 0; i < CS; ++i) mbar_init(&coef_empty[i], 1 + 128);
+    for (int i = 0; i < 2; ++i) { mbar_init(&acc_full[i], 1); mbar_init(&acc_empty[i], 128); }
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  {
+    // tile_centre over the 128 query rows: computed by warps 4-7 only
+    float xq[N];
+#pragma unroll
+    for (int d = 0; d < N; ++d) xq[d] = active ? a.x[(q0 + qrow) * N + d] : 0.0f;
+    if (is_epi) {
+#pragma unroll
+      for (int d = 0; d < N; ++d) {
+        float lo = active ? xq[d] : INFINITY, hi = active ? xq[d] : -INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+          hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) {
+          sred[((warp - 4) * N + d) * 2] = lo;
+          sred[((warp - 4) * N + d) * 2 + 1] = hi;
+        }
+      }
+    }
+    __syncthreads();
+    if (tid < N) {
+      float lo = INFINITY, hi = -INFINITY;
+      for (int w = 0; w < 4; ++w) {
+        lo = fminf(lo, sred[(w * N + tid) * 2]);
+        hi = fmaxf(hi, sred[(w * N + tid) * 2 + 1]);
+      }
+      sctr[tid] = (lo <= hi) ? 0.5f * (lo + hi) : 0.0f;
+    }
+    __syncthreads();
+    if (is_epi) {
+      float xt[N];
+#pragma unroll
+      for (int d = 0; d < N; ++d) xt[d] = active ? xq[d] - sctr[d] : 0.0f;
+      float phi[KP];
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) phi[tri(i) + j] = xt[i] * xt[j];
+#pragma unroll
+      for (int i = 0; i < N; ++i) phi[P + i] = xt[i];
+      phi[P + N] = active ? 1.0f : 0.0f;
+#pragma unroll
+      for (int k = P + N + 1; k < KP; ++k) phi[k] = 0.0f;
+      store_row_split<KP>(Ahi, Alo, qrow, S::SBO, phi);
+    }
+  }
+  if (warp == 4) {
+    tmem_alloc(&tmem_base, S::TMEM_COLS);
+    tmem_relinquish();
+  }
+  fence_proxy_async();
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  const long long beg = a.offsets[t], end = a.offsets[t + 1];
+  const int nchunks = (int)((end - beg + NC - 1) / NC);
+  volatile int* abort_flag = &s_abort;
+  auto fail = [&]() {
+    atomicExch(&s_abort, 1);
+    if (a.status) set_status(a.status, NDG_ERR_TIMEOUT);
+  };
+
+  if (warp == 8) {
+    // ---- loader
+    for (int i = 0; i < nchunks; ++i) {
+      const int r = i % RS;
+      int ok = 1;
+      if (lane == 0 && i >= RS)
+        ok = mbar_wait_or_abort(&rec_empty[r], ((i / RS) - 1) & 1, kWaitLimit, abort_flag);
+      ok = __shfl_sync(0xffffffffu, ok, 0);  // one decision for the whole warp
+      if (!ok) {
+        if (lane == 0) fail();
+        break;
+      }
+      const long long c0 = beg + (long long)i * NC;
+      const int n = (int)(end - c0 < NC ? end - c0 : NC);
+      // each lane copies its candidates' records as 16-byte cp.async
+      // transfers; its arrive on rec_full[r] fires when they have landed
+#pragma unroll
+      for (int u = 0; u < (NC + 31) / 32; ++u) {
+        const int j = lane + 32 * u;
+        if (j >= NC) continue;
+        const int gi = j < n ? a.ids[c0 + j] : -1;
+        const int g = ((unsigned)gi < (unsigned)a.Ge) ? gi : -1;
+        Ids[r * NC + j] = g;
+        if (g >= 0) {
+          const uint8_t* src = reinterpret_cast<const uint8_t*>(a.rec) + (size_t)g * S::RB;
+          uint8_t* dst = Rst + r * S::R_STAGE + (uint32_t)j * S::RB;
+#pragma unroll
+          for (uint32_t k = 0; k < S::RB; k += 16) cp_async16(dst + k, src + k);
+        }
+      }
+      __threadfence_block();  // the index stores before the (deferred) arrive
+      cp_async_arrive(&rec_full[r]);
+    }
+  } else if (warp < 4) {
+    // ---- builders (thread j = tid) and the MMA issuer (tid 0)
+    const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo);
+    constexpr uint32_t IDESC = idesc_tf32(NC);
+    for (int i = 0; i < nchunks; ++i) {
+      const int r = i % RS, sidx = i % CS, b = i & 1;
+      bool ok = mbar_wait_or_abort(&rec_full[r], (i / RS) & 1, kWaitLimit, abort_flag);
+      if (ok && i >= CS)
+        ok = mbar_wait_or_abort(&coef_empty[sidx], ((i / CS) - 1) & 1, kWaitLimit, abort_flag);
+      if (!ok) fail();
+      uint8_t* st = Cst + sidx * S::C_STAGE;
+      if (ok && tid < NC) {
+        const int g = Ids[r * NC + tid];
+        float4 rec[R / 4];
+        const float4* src = reinterpret_cast<const float4*>(Rst + r * S::R_STAGE + (uint32_t)tid * S::RB);
+#pragma unroll
+        for (int k = 0; k < R / 4; ++k) rec[k] = g >= 0 ? src[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+        stage_coef_ws<N>(rec, tid, sctr, st, st + S::B_BYTES,
+                         reinterpret_cast<float*>(st + 2 * S::B_BYTES));
+      }
+      mbar_arrive(&rec_empty[r]);
+      fence_proxy_async();
+      // named barrier over the 4 builder warps with an OR of the abort
+      // state: every builder takes the same branch
+      uint32_t quit;
+      asm volatile(
+          "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, 128, q;\n"
+          " selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(quit)
+          : "r"((uint32_t)(!ok || *abort_flag))
+          : "memory");
+      if (quit) break;
+      if (tid == 0) {
+        if (i >= 2 && !mbar_wait_or_abort(&acc_empty[b], ((i >> 1) - 1) & 1, kWaitLimit, abort_flag)) {
+          fail();
+        } else {
+          fence_after_sync();
+          const uint32_t d = tmem + (uint32_t)(b * NC);
+          const uint32_t bh = smem_u32(st), bl = smem_u32(st + S::B_BYTES);
+#pragma unroll
+          for (int ks = 0; ks < KP / 8; ++ks) {
+            const uint32_t ko = (uint32_t)ks * 256u;
+            const uint64_t dah = smem_desc(ah + ko, 128, S::SBO);
+            const uint64_t dal = smem_desc(al + ko, 128, S::SBO);
+            const uint64_t dbh = smem_desc(bh + ko, 128, S::SBO);
+            const uint64_t dbl = smem_desc(bl + ko, 128, S::SBO);
+            mma_tf32(d, dah, dbh, IDESC, ks > 0 ? 1u : 0u);
+            mma_tf32(d, dah, dbl, IDESC, 1u);
+            mma_tf32(d, dal, dbh, IDESC, 1u);
+          }
+          mma_commit(&acc_full[b]);
+          mma_commit(&coef_empty[sidx]);
+        }
+      }
+    }
+  } else {
+    // ---- epilogue (warps 4-7)
+    const uint32_t lane_off = (uint32_t)((warp - 4) * 32) << 16;
+    float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    for (int i = 0; i < nchunks; ++i) {
+      const int sidx = i % CS, b = i & 1;
+      if (!mbar_wait_or_abort(&acc_full[b], (i >> 1) & 1, kWaitLimit, abort_flag)) {
+        fail();
+        break;
+      }
+      fence_after_sync();
+      uint32_t v[NC];
+#pragma unroll
+      for (int cb = 0; cb < NC; cb += 32)
+        tmem_ld32_nowait(tmem + lane_off + (uint32_t)(b * NC + cb), v + cb);
+      tmem_wait_ld();
+      fence_before_sync();
+      mbar_arrive(&acc_empty[b]);
+      const float* sw2 = reinterpret_cast<const float*>(Cst + sidx * S::C_STAGE + 2 * S::B_BYTES);
+#pragma unroll
+      for (int j = 0; j < NC; j += 2) {
+        const float2 e = make_float2(ex2_approx(__uint_as_float(v[j])),
+                                     ex2_approx(__uint_as_float(v[j + 1])));
+        const float4 w01 = *reinterpret_cast<const float4*>(sw2 + (j >> 1) * 8);
+        const float2 w2p = *reinterpret_cast<const float2*>(sw2 + (j >> 1) * 8 + 4);
+        acc[0] = __ffma2_rn(make_float2(w01.x, w01.y), e, acc[0]);
+        acc[1] = __ffma2_rn(make_float2(w01.z, w01.w), e, acc[1]);
+        acc[2] = __ffma2_rn(w2p, e, acc[2]);
+      }
+      mbar_arrive(&coef_empty[sidx]);
+    }
+    if (active && !*abort_flag) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) a.y[(q0 + qrow) * 3 + c] = acc[c].x + acc[c].y;
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (*abort_flag) {
+    // let copies and MMAs still in flight finish before the CTA releases its memory
+    if (tid == 0) {
+      for (int i = 0; i < 2; ++i) mbar_wait_bounded(&acc_full[i], 0, kWaitLimit >> 4);
+    }
+    __syncthreads();
+  }
+  if (warp == 4) {
+    fence_after_sync();
+    tmem_dealloc(tmem, S::TMEM_COLS);
   }
 }
 
@@ -727,9 +1158,9 @@ int launch_fwd_tc(int N, const FwdArgs& a, long long T, cudaStream_t s) {
   const long long blocks = T * ((a.tile + 127) / 128);
 #define L_TC(n)                                                                              \
   {                                                                                          \
-    cudaFuncSetAttribute(fwd_tc_kernel<n>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
-                         (int)TcShape<n>::SMEM);                                             \
-    fwd_tc_kernel<n><<<(unsigned)blocks, 128, TcShape<n>::SMEM, s>>>(a);                     \
+    cudaFuncSetAttribute(fwd_tcws_kernel<n>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                         (int)WsShape<n>::SMEM);                                             \
+    fwd_tcws_kernel<n><<<(unsigned)blocks, 288, WsShape<n>::SMEM, s>>>(a);                   \
   }
   NDG_SWITCH_N(N, L_TC)
 #undef L_TC

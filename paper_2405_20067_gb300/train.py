@@ -37,7 +37,7 @@ class NDGEval(torch.autograd.Function):
         grad = ndg.Mixture(mix.N, mix.G, *[None if getattr(mix, f) is None
                                            else torch.empty_like(getattr(mix, f))
                                            for f in _PARAMS], has_children=mix.has_children)
-        mode = getattr(ev, "mode", ndg.NDG_MODE_FP32)
+        mode = getattr(ev, "bwd_mode", ndg.NDG_MODE_FP32)
         if mode == ndg.NDG_MODE_TC and mix.N > 6:
             mode = ndg.NDG_MODE_FP32  # the tensor-core backward covers N <= 6
         ndg.backward(mix, ev.x, ev.tile, ev.cull, dy.contiguous(), grad, ev.ws, mode=mode,
@@ -60,10 +60,13 @@ class Trainer:
 
     def __init__(self, mix: ndg.Mixture, x: torch.Tensor, target: torch.Tensor, tile: int,
                  cp: ndg.CullParams, lr: float = 1e-3, t: float = 0.01, phase: int = 300,
-                 E_cap: int | None = None, seed: int = 0, mode: int = ndg.NDG_MODE_FP32):
-        """mode: NDG_MODE_FP32 or NDG_MODE_TC (lifted tensor-core forward, and
-        backward for N <= 6)."""
+                 E_cap: int | None = None, seed: int = 0, mode: int = ndg.NDG_MODE_FP32,
+                 bwd_mode: int | None = None):
+        """mode / bwd_mode: NDG_MODE_FP32 or NDG_MODE_TC for the forward and
+        the backward (the tensor-core backward covers N <= 6); bwd_mode
+        defaults to mode."""
         self.mix, self.tile, self.cp, self.mode = mix, tile, cp, mode
+        self.bwd_mode = mode if bwd_mode is None else bwd_mode
         self.lr, self.t, self.phase = lr, t, phase
         for f in _PARAMS:
             p = getattr(mix, f)
@@ -96,7 +99,7 @@ class Trainer:
         """traces: dict name -> ndg.Trace for build_cull / forward / loss /
         backward / adam / densify, or None."""
         self.traces = traces
-        self.ev.mode = self.mode
+        self.ev.mode, self.ev.bwd_mode = self.mode, self.bwd_mode
         self.ev.trace_fwd = traces.get("forward") if traces else None
         self.ev.trace_bwd = traces.get("backward") if traces else None
 
@@ -112,7 +115,7 @@ class Trainer:
         if target is not None:
             self.target.copy_(target, non_blocking=True)
         mix = self.mix
-        self.ev.mode = self.mode
+        self.ev.mode, self.ev.bwd_mode = self.mode, self.bwd_mode
         ndg.build_cull(mix, self.x, self.tile, self.cp, self.ev.cull, self.ev.ws,
                        trace=self._tr("build_cull"))
         with torch.enable_grad():
