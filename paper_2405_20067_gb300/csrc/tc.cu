@@ -28,196 +28,10 @@
 #include "common.cuh"
 #include "internal.h"
 #include "kernels.h"
+#include "tcgen05.cuh"
 
 namespace ndg {
 
-namespace {
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
-               "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void fence_before_sync() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_after_sync() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: false after `limit` unsuccessful polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
-  for (uint32_t i = 0; i < limit; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-// 16-byte asynchronous copy global -> shared (L2 only), and an arrive on
-// `bar` once all of this thread's earlier cp.async copies have landed (the
-// barrier's expected count includes this arrival).
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-// Bounded wait that gives up early once another thread has raised *abort.
-__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, uint32_t limit,
-                                                   volatile int* abort) {
-  for (uint32_t i = 0; i < limit; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 1023u) == 1023u && *abort) return false;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
-      "%30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// x32 load without the wait (several may be in flight; tmem_wait_ld() ends them).
-__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
-      "%30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr)
-      : "memory");
-}
-__device__ __forceinline__ void tmem_wait_ld() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Matrix descriptor: no swizzle; addresses and offsets in 16-byte units.
-// lbo: byte distance between core matrices along K; sbo: along M / N.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
-         ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
-}
-
-// Instruction descriptor for kind::tf32: F32 accumulator, TF32 A and B, both
-// K-major (TF32 operands cannot be MN-major), M = 128, N = n.
-__host__ __device__ constexpr uint32_t idesc_tf32(int n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
-}
-
-__device__ __forceinline__ float tf32_hi(float v) {
-  uint32_t h;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
-  return __uint_as_float(h);
-}
-
-// Byte offset of element (row, k) in the K-major no-swizzle layout.
-__device__ __forceinline__ uint32_t kmajor_off(int row, int k, uint32_t sbo) {
-  return (uint32_t)(row >> 3) * sbo + (uint32_t)(k >> 2) * 128u + (uint32_t)(row & 7) * 16u +
-         (uint32_t)(k & 3) * 4u;
-}
-
-// Writes one K-major row (KP values, multiple of 4) split into hi / lo.
-template <int KP>
-__device__ __forceinline__ void store_row_split(uint8_t* hi, uint8_t* lo, int row, uint32_t sbo,
-                                                const float (&v)[KP]) {
-#pragma unroll
-  for (int k = 0; k < KP; k += 4) {
-    float4 h, l;
-    h.x = tf32_hi(v[k]); l.x = v[k] - h.x;
-    h.y = tf32_hi(v[k + 1]); l.y = v[k + 1] - h.y;
-    h.z = tf32_hi(v[k + 2]); l.z = v[k + 2] - h.z;
-    h.w = tf32_hi(v[k + 3]); l.w = v[k + 3] - h.w;
-    const uint32_t off = kmajor_off(row, k, sbo);
-    *reinterpret_cast<float4*>(hi + off) = h;
-    *reinterpret_cast<float4*>(lo + off) = l;
-  }
-}
-
-constexpr float kNegHalfLog2eTC = -0.72134752044448170368f;
-constexpr uint32_t kWaitLimit = 1u << 26;
-
-}  // namespace
 
 template <int N>
 struct TcShape {
@@ -299,12 +113,6 @@ __device__ __forceinline__ void stage_coef(const float4 (&rec)[rec_floats(N) / 4
   d[2] = buf[P + N + 1];
   d[4] = buf[P + N + 2];
 }
-
-// As stage_coef, for the warp-specialised kernel's stage layout.
-template <int N>
-__device__ __forceinline__ void stage_coef_ws(const float4 (&rec)[rec_floats(N) / 4], int j,
-                                              const float* __restrict__ sctr, uint8_t* Bhi,
-                                              uint8_t* Blo, float* sw2);
 
 template <int N>
 __global__ void __launch_bounds__(128) fwd_tc_kernel(FwdArgs a) {
@@ -469,326 +277,6 @@ __global__ void __launch_bounds__(128) fwd_tc_kernel(FwdArgs a) {
   fence_before_sync();
   __syncthreads();
   if (warp == 0) {
-    fence_after_sync();
-    tmem_dealloc(tmem, S::TMEM_COLS);
-  }
-}
-
-// ---- warp-specialised forward ------------------------------------------------------
-// Same arithmetic as above, organised as a pipeline inside the CTA (one CTA
-// per 128-query block):
-//   warp 8      loader: reads the chunk's candidate indices and gathers their
-//               prepared records into a ring of RS shared-memory stages with
-//               16-byte cp.async copies (completion on rec_full[r]);
-//   warps 0-3   builders: one candidate each; turn a record stage into a
-//               coefficient stage (split TF32 hi/lo, CS stages) and release
-//               the record stage; after a named barrier, thread 0 issues the
-//               chunk's MMAs into one of two TMEM accumulators and commits to
-//               acc_full[b] and coef_empty[s];
-//   warps 4-7   epilogue: one query row each (TMEM lanes 32 (w % 4) + lane);
-//               read the accumulator, release it (acc_empty[b]), then
-//               exp2 + weighted RGB sum with the stage's weights, release the
-//               coefficient stage (coef_empty[s]).
-// Every wait is bounded and gives up once any thread has timed out.
-template <int N>
-struct WsShape {
-  static constexpr int P = tri(N);
-  static constexpr int F = P + N + 1;
-  static constexpr int KP = (F + 7) / 8 * 8;
-  static constexpr int NC = N <= 6 ? 128 : (N <= 10 ? 64 : 32);
-  static constexpr int R = rec_floats(N);
-  static constexpr uint32_t RB = (uint32_t)R * 4;  // bytes per record (multiple of 16)
-  static constexpr int CS = N <= 6 ? 3 : 2;        // coefficient stages
-  static constexpr int RS = N <= 6 ? 4 : (N <= 10 ? 3 : 2);  // record stages
-  static constexpr uint32_t SBO = (KP / 4) * 128;
-  static constexpr uint32_t A_BYTES = 128u * KP * 4;
-  static constexpr uint32_t B_BYTES = (uint32_t)NC * KP * 4;
-  static constexpr uint32_t W_BYTES = (uint32_t)NC * 16;
-  static constexpr uint32_t C_STAGE = 2 * B_BYTES + W_BYTES;
-  static constexpr uint32_t R_STAGE = (uint32_t)NC * RB;
-  static constexpr uint32_t ID_BYTES = (uint32_t)NC * 4;
-  static constexpr uint32_t TMEM_COLS = 2 * NC;
-  static constexpr uint32_t SMEM_USED =
-      2 * A_BYTES + CS * C_STAGE + RS * (R_STAGE + ID_BYTES) + 128;
-  static constexpr uint32_t SMEM_FLOOR = (228u * 1024u) / (512u / TMEM_COLS + 1) + 1024u;
-  static constexpr uint32_t SMEM = SMEM_USED > SMEM_FLOOR ? SMEM_USED : SMEM_FLOOR;
-  static_assert(SMEM <= 227u * 1024u, "shared memory");
-};
-
-template <int N>
-__device__ __forceinline__ void stage_coef_ws(const float4 (&rec)[rec_floats(N) / 4], int j,
-                                              const float* __restrict__ sctr, uint8_t* Bhi,
-                                              uint8_t* Blo, float* sw2) {
-  using S = WsShape<N>;
-  constexpr int P = S::P, KP = S::KP, R = rec_floats(N), R4 = R / 4;
-  float buf[R];
-#pragma unroll
-  for (int i = 0; i < R4; ++i) {
-    buf[4 * i] = rec[i].x; buf[4 * i + 1] = rec[i].y; buf[4 * i + 2] = rec[i].z; buf[4 * i + 3] = rec[i].w;
-  }
-  float coef[KP];
-  float mt[N];
-#pragma unroll
-  for (int i = 0; i < N; ++i) mt[i] = buf[P + i] - sctr[i];
-  float cst = 0.0f;
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    float sacc = 0.0f;
-#pragma unroll
-    for (int k = 0; k < N; ++k) sacc = fmaf(buf[i >= k ? tri(i) + k : tri(k) + i], mt[k], sacc);
-    coef[P + i] = kNegHalfLog2eTC * (-2.0f * sacc);
-    cst = fmaf(mt[i], sacc, cst);
-  }
-#pragma unroll
-  for (int i = 0; i < N; ++i)
-#pragma unroll
-    for (int k = 0; k <= i; ++k)
-      coef[tri(i) + k] = kNegHalfLog2eTC * (i == k ? buf[tri(i) + k] : 2.0f * buf[tri(i) + k]);
-  coef[P + N] = kNegHalfLog2eTC * cst;
-#pragma unroll
-  for (int k = P + N + 1; k < KP; ++k) coef[k] = 0.0f;
-  store_row_split<KP>(Bhi, Blo, j, S::SBO, coef);
-  float* d = sw2 + (j >> 1) * 8 + (j & 1);
-  d[0] = buf[P + N];
-  d[2] = buf[P + N + 1];
-  d[4] = buf[P + N + 2];
-}
-
-template <int N>
-__global__ void __launch_bounds__(288, 1) fwd_tcws_kernel(FwdArgs a) {
-  using S = WsShape<N>;
-  constexpr int P = S::P, KP = S::KP, NC = S::NC, CS = S::CS, RS = S::RS, R = S::R;
-  extern __shared__ __align__(128) uint8_t dsm[];
-  uint8_t* base = (uint8_t*)(((uintptr_t)dsm + 127) & ~(uintptr_t)127);
-  uint8_t* Ahi = base;
-  uint8_t* Alo = Ahi + S::A_BYTES;
-  uint8_t* Cst = Alo + S::A_BYTES;           // CS stages of (Bhi, Blo, w pairs)
-  uint8_t* Rst = Cst + CS * S::C_STAGE;      // RS stages of records
-  int* Ids = reinterpret_cast<int*>(Rst + RS * S::R_STAGE);  // RS stages of indices
-  __shared__ uint64_t rec_full[RS], rec_empty[RS], coef_empty[CS], acc_full[2], acc_empty[2];
-  __shared__ uint32_t tmem_base;
-  __shared__ float sred[4 * N * 2];
-  __shared__ float sctr[N];
-  __shared__ int s_abort;
-
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int halves = (a.tile + 127) >> 7;
-  const long long t = blockIdx.x / halves;
-  const int half = blockIdx.x - (int)(t * halves);
-  const long long qt = t * a.tile;
-  const long long q0 = qt + half * 128;
-  const long long qend_tile = qt + a.tile < a.Q ? qt + a.tile : a.Q;
-  const int nq = (int)(qend_tile - q0 < 128 ? qend_tile - q0 : 128);
-  const bool is_epi = warp >= 4 && warp < 8;
-  const int qrow = tid - 128;  // epilogue: query row (TMEM lane)
-  const bool active = is_epi && qrow < nq;
-
-  // ---- setup: centre (from the epilogue warps' queries), Phi rows, barriers, TMEM
-  if (tid == 0) {
-    for (int i = 0; i < RS; ++i) { mbar_init(&rec_full[i], 32); mbar_init(&rec_empty[i], 128); }
-    for (int i = 0; i < CS; ++i) mbar_init(&coef_empty[i], 1 + 128);
-    for (int i = 0; i < 2; ++i) { mbar_init(&acc_full[i], 1); mbar_init(&acc_empty[i], 128); }
-    s_abort = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  {
-    // tile_centre over the 128 query rows: computed by warps 4-7 only
-    float xq[N];
-#pragma unroll
-    for (int d = 0; d < N; ++d) xq[d] = active ? a.x[(q0 + qrow) * N + d] : 0.0f;
-    if (is_epi) {
-#pragma unroll
-      for (int d = 0; d < N; ++d) {
-        float lo = active ? xq[d] : INFINITY, hi = active ? xq[d] : -INFINITY;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-          hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-        }
-        if (lane == 0) {
-          sred[((warp - 4) * N + d) * 2] = lo;
-          sred[((warp - 4) * N + d) * 2 + 1] = hi;
-        }
-      }
-    }
-    __syncthreads();
-    if (tid < N) {
-      float lo = INFINITY, hi = -INFINITY;
-      for (int w = 0; w < 4; ++w) {
-        lo = fminf(lo, sred[(w * N + tid) * 2]);
-        hi = fmaxf(hi, sred[(w * N + tid) * 2 + 1]);
-      }
-      sctr[tid] = (lo <= hi) ? 0.5f * (lo + hi) : 0.0f;
-    }
-    __syncthreads();
-    if (is_epi) {
-      float xt[N];
-#pragma unroll
-      for (int d = 0; d < N; ++d) xt[d] = active ? xq[d] - sctr[d] : 0.0f;
-      float phi[KP];
-#pragma unroll
-      for (int i = 0; i < N; ++i)
-#pragma unroll
-        for (int j = 0; j <= i; ++j) phi[tri(i) + j] = xt[i] * xt[j];
-#pragma unroll
-      for (int i = 0; i < N; ++i) phi[P + i] = xt[i];
-      phi[P + N] = active ? 1.0f : 0.0f;
-#pragma unroll
-      for (int k = P + N + 1; k < KP; ++k) phi[k] = 0.0f;
-      store_row_split<KP>(Ahi, Alo, qrow, S::SBO, phi);
-    }
-  }
-  if (warp == 4) {
-    tmem_alloc(&tmem_base, S::TMEM_COLS);
-    tmem_relinquish();
-  }
-  fence_proxy_async();
-  fence_before_sync();
-  __syncthreads();
-  fence_after_sync();
-  const uint32_t tmem = tmem_base;
-  const long long beg = a.offsets[t], end = a.offsets[t + 1];
-  const int nchunks = (int)((end - beg + NC - 1) / NC);
-  volatile int* abort_flag = &s_abort;
-  auto fail = [&]() {
-    atomicExch(&s_abort, 1);
-    if (a.status) set_status(a.status, NDG_ERR_TIMEOUT);
-  };
-
-  if (warp == 8) {
-    // ---- loader
-    for (int i = 0; i < nchunks; ++i) {
-      const int r = i % RS;
-      int ok = 1;
-      if (lane == 0 && i >= RS)
-        ok = mbar_wait_or_abort(&rec_empty[r], ((i / RS) - 1) & 1, kWaitLimit, abort_flag);
-      ok = __shfl_sync(0xffffffffu, ok, 0);  // one decision for the whole warp
-      if (!ok) {
-        if (lane == 0) fail();
-        break;
-      }
-      const long long c0 = beg + (long long)i * NC;
-      const int n = (int)(end - c0 < NC ? end - c0 : NC);
-      // each lane copies its candidates' records as 16-byte cp.async
-      // transfers; its arrive on rec_full[r] fires when they have landed
-#pragma unroll
-      for (int u = 0; u < (NC + 31) / 32; ++u) {
-        const int j = lane + 32 * u;
-        if (j >= NC) continue;
-        const int gi = j < n ? a.ids[c0 + j] : -1;
-        const int g = ((unsigned)gi < (unsigned)a.Ge) ? gi : -1;
-        Ids[r * NC + j] = g;
-        if (g >= 0) {
-          const uint8_t* src = reinterpret_cast<const uint8_t*>(a.rec) + (size_t)g * S::RB;
-          uint8_t* dst = Rst + r * S::R_STAGE + (uint32_t)j * S::RB;
-#pragma unroll
-          for (uint32_t k = 0; k < S::RB; k += 16) cp_async16(dst + k, src + k);
-        }
-      }
-      __threadfence_block();  // the index stores before the (deferred) arrive
-      cp_async_arrive(&rec_full[r]);
-    }
-  } else if (warp < 4) {
-    // ---- builders (thread j = tid) and the MMA issuer (tid 0)
-    const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo);
-    constexpr uint32_t IDESC = idesc_tf32(NC);
-    for (int i = 0; i < nchunks; ++i) {
-      const int r = i % RS, sidx = i % CS, b = i & 1;
-      bool ok = mbar_wait_or_abort(&rec_full[r], (i / RS) & 1, kWaitLimit, abort_flag);
-      if (ok && i >= CS)
-        ok = mbar_wait_or_abort(&coef_empty[sidx], ((i / CS) - 1) & 1, kWaitLimit, abort_flag);
-      if (!ok) fail();
-      uint8_t* st = Cst + sidx * S::C_STAGE;
-      if (ok && tid < NC) {
-        const int g = Ids[r * NC + tid];
-        float4 rec[R / 4];
-        const float4* src = reinterpret_cast<const float4*>(Rst + r * S::R_STAGE + (uint32_t)tid * S::RB);
-#pragma unroll
-        for (int k = 0; k < R / 4; ++k) rec[k] = g >= 0 ? src[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-        stage_coef_ws<N>(rec, tid, sctr, st, st + S::B_BYTES,
-                         reinterpret_cast<float*>(st + 2 * S::B_BYTES));
-      }
-      mbar_arrive(&rec_empty[r]);
-      fence_proxy_async();
-      // named barrier over the 4 builder warps with an OR of the abort
-      // state: every builder takes the same branch
-      uint32_t quit;
-      asm volatile(
-          "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, 128, q;\n"
-          " selp.u32 %0, 1, 0, p;\n}"
-          : "=r"(quit)
-          : "r"((uint32_t)(!ok || *abort_flag))
-          : "memory");
-      if (quit) break;
-      if (tid == 0) {
-        if (i >= 2 && !mbar_wait_or_abort(&acc_empty[b], ((i >> 1) - 1) & 1, kWaitLimit, abort_flag)) {
-          fail();
-        } else {
-          fence_after_sync();
-          const uint32_t d = tmem + (uint32_t)(b * NC);
-          const uint32_t bh = smem_u32(st), bl = smem_u32(st + S::B_BYTES);
-#pragma unroll
-          for (int ks = 0; ks < KP / 8; ++ks) {
-            const uint32_t ko = (uint32_t)ks * 256u;
-            const uint64_t dah = smem_desc(ah + ko, 128, S::SBO);
-            const uint64_t dal = smem_desc(al + ko, 128, S::SBO);
-            const uint64_t dbh = smem_desc(bh + ko, 128, S::SBO);
-            const uint64_t dbl = smem_desc(bl + ko, 128, S::SBO);
-            mma_tf32(d, dah, dbh, IDESC, ks > 0 ? 1u : 0u);
-            mma_tf32(d, dah, dbl, IDESC, 1u);
-            mma_tf32(d, dal, dbh, IDESC, 1u);
-          }
-          mma_commit(&acc_full[b]);
-          mma_commit(&coef_empty[sidx]);
-        }
-      }
-    }
-  } else {
-    // ---- epilogue (warps 4-7)
-    const uint32_t lane_off = (uint32_t)((warp - 4) * 32) << 16;
-    float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    for (int i = 0; i < nchunks; ++i) {
-      const int sidx = i % CS, b = i & 1;
-      if (!mbar_wait_or_abort(&acc_full[b], (i >> 1) & 1, kWaitLimit, abort_flag)) {
-        fail();
-        break;
-      }
-      fence_after_sync();
-      uint32_t v[NC];
-#pragma unroll
-      for (int cb = 0; cb < NC; cb += 32)
-        tmem_ld32_nowait(tmem + lane_off + (uint32_t)(b * NC + cb), v + cb);
-      tmem_wait_ld();
-      fence_before_sync();
-      mbar_arrive(&acc_empty[b]);
-      const float* sw2 = reinterpret_cast<const float*>(Cst + sidx * S::C_STAGE + 2 * S::B_BYTES);
-#pragma unroll
-      for (int j = 0; j < NC; j += 2) {
-        const float2 e = make_float2(ex2_approx(__uint_as_float(v[j])),
-                                     ex2_approx(__uint_as_float(v[j + 1])));
-        const float4 w01 = *reinterpret_cast<const float4*>(sw2 + (j >> 1) * 8);
-        const float2 w2p = *reinterpret_cast<const float2*>(sw2 + (j >> 1) * 8 + 4);
-        acc[0] = __ffma2_rn(make_float2(w01.x, w01.y), e, acc[0]);
-        acc[1] = __ffma2_rn(make_float2(w01.z, w01.w), e, acc[1]);
-        acc[2] = __ffma2_rn(w2p, e, acc[2]);
-      }
-      mbar_arrive(&coef_empty[sidx]);
-    }
-    if (active && !*abort_flag) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) a.y[(q0 + qrow) * 3 + c] = acc[c].x + acc[c].y;
-    }
-  }
-  fence_before_sync();
-  __syncthreads();
-  if (*abort_flag) {
-    // let copies and MMAs still in flight finish before the CTA releases its memory
-    if (tid == 0) {
-      for (int i = 0; i < 2; ++i) mbar_wait_bounded(&acc_full[i], 0, kWaitLimit >> 4);
-    }
-    __syncthreads();
-  }
-  if (warp == 4) {
     fence_after_sync();
     tmem_dealloc(tmem, S::TMEM_COLS);
   }
@@ -1155,14 +643,18 @@ __global__ void __launch_bounds__(128, 1) bwd_tc_kernel(BwdArgs a) {
 
 int launch_fwd_tc(int N, const FwdArgs& a, long long T, cudaStream_t s) {
   if (T <= 0) return 0;
+  if (N <= 8) return launch_fwd_h(N, a, T, s);  // FP16-split kernel
   const long long blocks = T * ((a.tile + 127) / 128);
 #define L_TC(n)                                                                              \
   {                                                                                          \
-    cudaFuncSetAttribute(fwd_tcws_kernel<n>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                         (int)WsShape<n>::SMEM);                                             \
-    fwd_tcws_kernel<n><<<(unsigned)blocks, 288, WsShape<n>::SMEM, s>>>(a);                   \
+    cudaFuncSetAttribute(fwd_tc_kernel<n>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                         (int)TcShape<n>::SMEM);                                             \
+    fwd_tc_kernel<n><<<(unsigned)blocks, 128, TcShape<n>::SMEM, s>>>(a);                     \
   }
-  NDG_SWITCH_N(N, L_TC)
+  switch (N) {
+    NDG_CASE_N(9, L_TC) NDG_CASE_N(10, L_TC) NDG_CASE_N(11, L_TC) NDG_CASE_N(12, L_TC)
+    default: return 0;
+  }
 #undef L_TC
   return 1;
 }
