@@ -26,11 +26,13 @@
 //               After a named barrier thread 0 issues the chunk's MMAs into
 //               accumulator buffer i & 1 and commits them to acc_full and
 //               coef_empty;
-//   warps 4-11  epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its
-//               query rows r and r + 128), columns 64 ((w - 4) / 4) .. + 63
-//               (half of the candidates), forms e = 2^s and accumulates w e;
-//               the two column halves are summed through shared memory at
-//               the end.
+//   warps 4-11  epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of both
+//               row blocks (query rows r and r + 128), columns 64 ((w - 4) / 4)
+//               .. + 63 (half of the candidates), with the 16x256b load shape
+//               (a thread holds 8 rows x 8 columns of each 32-column block),
+//               forms e = 2^s and accumulates w e; partial row sums are
+//               combined with shuffles and, across the two column halves,
+//               through shared memory at the end.
 // Barrier operations are one per warp (an elected lane), and every wait is
 // bounded: on a timeout the kernel records NDG_ERR_TIMEOUT, lets the issued
 // MMAs finish (bounded), frees its tensor memory and returns.
@@ -300,7 +302,7 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
       // every builder takes the same branch
       if (bar_red_or(1, 128, !ok || *abort_flag)) break;
       if (tid == 0) {
-        if (i >= 2 && !mbar_wait_or_abort(&acc_empty[b], ((i >> 1) - 1) & 1, kWaitLimit, abort_flag)) {
+        if (i >= 2 && !mbar_wait_sleep(&acc_empty[b], ((i >> 1) - 1) & 1, abort_flag)) {
           fail();
         } else {
           fence_after_sync();
@@ -326,12 +328,18 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
       }
     }
   } else {
-    // ---- epilogue
+    // ---- epilogue (tcgen05.ld 16x256b: thread t holds lanes t/4 and t/4 + 8
+    // of a 16-lane group at columns 2 (t % 4) + {0, 1} of every 8-column group,
+    // so each weight load serves eight query rows)
     const int quad = warp & 3, grp = (warp - 4) >> 2;
-    const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
-    const int r0 = quad * 32 + lane;  // rows r0 (block 0) and r0 + 128 (block 1)
-    float2 acc0[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    float2 acc1[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    const int tq = lane & 3, tr = lane >> 2;
+    // rows ri = rb * 4 + hb * 2 + s: row block rb, 16-lane group hb, lane t/4 + 8 s;
+    // .x / .y accumulate the even / odd column of the thread's pairs
+    float2 acc[8][3];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[r][c] = make_float2(0.f, 0.f);
     for (int i = 0; i < nchunks; ++i) {
       const int s = i % CS, b = i & 1;
       bool ok = warp_wait(&acc_full[b], (i >> 1) & 1, abort_flag);
@@ -343,74 +351,82 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
       fence_after_sync();
       const int4 fl = *reinterpret_cast<const int4*>(&sflag[s][0]);
       const bool scaled = (fl.x | fl.y | fl.z | fl.w) != 0;
+      // weight pair entries of this thread: p = 32 grp + cb / 2 + 4 k + tq
       const float* wp = reinterpret_cast<const float*>(Cst + s * S::C_STAGE + 2 * S::B_BYTES) +
-                        grp * 32 * 8;
+                        (grp * 32 + tq) * 8;
 #pragma unroll 1
       for (int cb = 0; cb < 64; cb += 32) {
-        uint32_t v0[32], v1[32];
-        const uint32_t col = tmem + lane_off + (uint32_t)(b * 256 + grp * 64 + cb);
-        tmem_ld32_nowait(col, v0);
-        if (nh > 1) tmem_ld32_nowait(col + 128u, v1);
+        uint32_t v[4][16];
+#pragma unroll
+        for (int rb = 0; rb < 2; ++rb)
+#pragma unroll
+          for (int hb = 0; hb < 2; ++hb)
+            tmem_ld16x256_x4_nowait(tmem + ((uint32_t)(quad * 32 + hb * 16) << 16) +
+                                        (uint32_t)(b * 256 + rb * 128 + grp * 64 + cb),
+                                    v[rb * 2 + hb]);
         tmem_wait_ld();
         if (cb == 32) {  // this warp's reads of buffer b are complete
           fence_before_sync();
           warp_arrive(&acc_empty[b]);
         }
-        const float* wq = wp + (cb >> 1) * 8;
-        if (nh > 1) {
 #pragma unroll
-          for (int c = 0; c < 32; c += 2) {
-            const float4 w01 = *reinterpret_cast<const float4*>(wq + (c >> 1) * 8);
-            const float4 w2k = *reinterpret_cast<const float4*>(wq + (c >> 1) * 8 + 4);
-            float2 s0 = make_float2(__uint_as_float(v0[c]), __uint_as_float(v0[c + 1]));
-            float2 s1 = make_float2(__uint_as_float(v1[c]), __uint_as_float(v1[c + 1]));
-            if (scaled) {
-              s0 = __fmul2_rn(s0, make_float2(w2k.z, w2k.w));
-              s1 = __fmul2_rn(s1, make_float2(w2k.z, w2k.w));
+        for (int k = 0; k < 4; ++k) {
+          const float* wk = wp + ((cb >> 1) + 4 * k) * 8;
+          const float4 w01 = *reinterpret_cast<const float4*>(wk);
+          const float2 w2 = *reinterpret_cast<const float2*>(wk + 4);
+          const float2 sc = scaled ? *reinterpret_cast<const float2*>(wk + 6) : make_float2(1.f, 1.f);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              float2 sv = make_float2(__uint_as_float(v[q][4 * k + 2 * h]),
+                                      __uint_as_float(v[q][4 * k + 2 * h + 1]));
+              if (scaled) sv = __fmul2_rn(sv, sc);
+              const float2 e = make_float2(ex2_approx(sv.x), ex2_approx(sv.y));
+              const int ri = q * 2 + h;
+              acc[ri][0] = __ffma2_rn(make_float2(w01.x, w01.y), e, acc[ri][0]);
+              acc[ri][1] = __ffma2_rn(make_float2(w01.z, w01.w), e, acc[ri][1]);
+              acc[ri][2] = __ffma2_rn(w2, e, acc[ri][2]);
             }
-            const float2 e0 = make_float2(ex2_approx(s0.x), ex2_approx(s0.y));
-            const float2 e1 = make_float2(ex2_approx(s1.x), ex2_approx(s1.y));
-            acc0[0] = __ffma2_rn(make_float2(w01.x, w01.y), e0, acc0[0]);
-            acc0[1] = __ffma2_rn(make_float2(w01.z, w01.w), e0, acc0[1]);
-            acc0[2] = __ffma2_rn(make_float2(w2k.x, w2k.y), e0, acc0[2]);
-            acc1[0] = __ffma2_rn(make_float2(w01.x, w01.y), e1, acc1[0]);
-            acc1[1] = __ffma2_rn(make_float2(w01.z, w01.w), e1, acc1[1]);
-            acc1[2] = __ffma2_rn(make_float2(w2k.x, w2k.y), e1, acc1[2]);
-          }
-        } else {
-#pragma unroll
-          for (int c = 0; c < 32; c += 2) {
-            const float4 w01 = *reinterpret_cast<const float4*>(wq + (c >> 1) * 8);
-            const float4 w2k = *reinterpret_cast<const float4*>(wq + (c >> 1) * 8 + 4);
-            float2 s0 = make_float2(__uint_as_float(v0[c]), __uint_as_float(v0[c + 1]));
-            if (scaled) s0 = __fmul2_rn(s0, make_float2(w2k.z, w2k.w));
-            const float2 e0 = make_float2(ex2_approx(s0.x), ex2_approx(s0.y));
-            acc0[0] = __ffma2_rn(make_float2(w01.x, w01.y), e0, acc0[0]);
-            acc0[1] = __ffma2_rn(make_float2(w01.z, w01.w), e0, acc0[1]);
-            acc0[2] = __ffma2_rn(make_float2(w2k.x, w2k.y), e0, acc0[2]);
-          }
         }
       }
       warp_arrive(&coef_empty[s]);
     }
-    // ---- sum the two column halves and write y
-    if (grp == 1) {
+    // ---- row sums: over the pair halves, the four threads sharing a lane
+    // (shuffles) and the two column groups (shared memory); write y
+    float rs[8][3];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        red[r0 * 4 + c] = acc0[c].x + acc0[c].y;
-        red[(r0 + 128) * 4 + c] = acc1[c].x + acc1[c].y;
+        float v = acc[r][c].x + acc[r][c].y;
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        rs[r][c] = v;
+      }
+    // thread tq owns rows ri = 2 tq, 2 tq + 1
+    auto row_of = [&](int ri) {
+      return (ri >> 2) * 128 + quad * 32 + ((ri >> 1) & 1) * 16 + (ri & 1) * 8 + tr;
+    };
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      if ((r >> 1) != tq) continue;
+      if (grp == 1) {
+        const int qr = row_of(r);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) red[qr * 4 + c] = rs[r][c];
       }
     }
     bar_sync(2, 256);
     if (grp == 0 && !*abort_flag) {
-      if (r0 < nq) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) a.y[(qt + r0) * 3 + c] = (acc0[c].x + acc0[c].y) + red[r0 * 4 + c];
-      }
-      if (r0 + 128 < nq) {
+      for (int r = 0; r < 8; ++r) {
+        if ((r >> 1) != tq) continue;
+        const int qr = row_of(r);
+        if (qr < nq) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-          a.y[(qt + r0 + 128) * 3 + c] = (acc1[c].x + acc1[c].y) + red[(r0 + 128) * 4 + c];
+          for (int c = 0; c < 3; ++c) a.y[(qt + qr) * 3 + c] = rs[r][c] + red[qr * 4 + c];
+        }
       }
     }
   }

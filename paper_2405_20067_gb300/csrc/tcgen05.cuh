@@ -148,6 +148,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16x256b.x4 load without the wait: 16 lanes x 32 columns.  Thread t gets,
+// for each 8-column group k, registers 4k, 4k+1 = lane t/4, columns
+// 8k + 2 (t % 4) + {0, 1}, and 4k+2, 4k+3 = lane t/4 + 8, same columns.
+__device__ __forceinline__ void tmem_ld16x256_x4_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.16x256b.x4.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+
 // Matrix descriptor: no swizzle; addresses and offsets in 16-byte units.
 // lbo: byte distance between core matrices along K; sbo: along M / N.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -210,11 +224,35 @@ __host__ __device__ constexpr uint32_t idesc_f16(int n) {
   return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
 }
 
-// Warp-level bounded wait: lane 0 polls, the outcome is broadcast, and the
+// try_wait with a suspend-time hint: the thread may sleep (up to the hint,
+// in nanoseconds) until the phase completes instead of spinning.
+constexpr uint32_t kSuspendNs = 20000;
+constexpr uint32_t kSleepLimit = 1u << 16;  // polls: at most ~1.3 s of suspension
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
+      : "memory");
+  return ok != 0;
+}
+// Bounded sleeping wait that gives up once another thread has raised *abort.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity,
+                                                volatile int* abort) {
+  for (uint32_t i = 0; i < kSleepLimit; ++i) {
+    if (mbar_try_wait_sleep(bar, parity)) return true;
+    if (*abort) return false;
+  }
+  return false;
+}
+
+// Warp-level bounded wait: lane 0 waits, the outcome is broadcast, and the
 // warp synchronises (memory ordering) before any lane reads guarded data.
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
   int ok = 1;
-  if ((threadIdx.x & 31) == 0) ok = mbar_wait_or_abort(bar, parity, kWaitLimit, abort) ? 1 : 0;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait_sleep(bar, parity, abort) ? 1 : 0;
   ok = __shfl_sync(0xffffffffu, ok, 0);
   __syncwarp();
   return ok != 0;
