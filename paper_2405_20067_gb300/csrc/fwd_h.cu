@@ -354,8 +354,9 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
       // weight pair entries of this thread: p = 32 grp + cb / 2 + 4 k + tq
       const float* wp = reinterpret_cast<const float*>(Cst + s * S::C_STAGE + 2 * S::B_BYTES) +
                         (grp * 32 + tq) * 8;
-#pragma unroll 1
-      for (int cb = 0; cb < 64; cb += 32) {
+      // one 32-column block of this warp's 64 (all four lane / row groups)
+      auto block = [&](int cb, auto sc_tag) {
+        constexpr bool SC = decltype(sc_tag)::value;
         uint32_t v[4][16];
 #pragma unroll
         for (int rb = 0; rb < 2; ++rb)
@@ -365,6 +366,8 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
                                         (uint32_t)(b * 256 + rb * 128 + grp * 64 + cb),
                                     v[rb * 2 + hb]);
         tmem_wait_ld();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tmem_reg_fence16(v[q]);
         if (cb == 32) {  // this warp's reads of buffer b are complete
           fence_before_sync();
           warp_arrive(&acc_empty[b]);
@@ -374,14 +377,15 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
           const float* wk = wp + ((cb >> 1) + 4 * k) * 8;
           const float4 w01 = *reinterpret_cast<const float4*>(wk);
           const float2 w2 = *reinterpret_cast<const float2*>(wk + 4);
-          const float2 sc = scaled ? *reinterpret_cast<const float2*>(wk + 6) : make_float2(1.f, 1.f);
+          float2 sc = make_float2(1.f, 1.f);
+          if (SC) sc = *reinterpret_cast<const float2*>(wk + 6);
 #pragma unroll
           for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               float2 sv = make_float2(__uint_as_float(v[q][4 * k + 2 * h]),
                                       __uint_as_float(v[q][4 * k + 2 * h + 1]));
-              if (scaled) sv = __fmul2_rn(sv, sc);
+              if (SC) sv = __fmul2_rn(sv, sc);
               const float2 e = make_float2(ex2_approx(sv.x), ex2_approx(sv.y));
               const int ri = q * 2 + h;
               acc[ri][0] = __ffma2_rn(make_float2(w01.x, w01.y), e, acc[ri][0]);
@@ -389,6 +393,11 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
               acc[ri][2] = __ffma2_rn(w2, e, acc[ri][2]);
             }
         }
+      };
+#pragma unroll 1
+      for (int cb = 0; cb < 64; cb += 32) {
+        if (scaled) block(cb, BoolTag<true>{});
+        else block(cb, BoolTag<false>{});
       }
       warp_arrive(&coef_empty[s]);
     }

@@ -162,6 +162,22 @@ __device__ __forceinline__ void tmem_ld16x256_x4_nowait(uint32_t taddr, uint32_t
       : "memory");
 }
 
+// Empty register fence: values loaded by an asynchronous tcgen05.ld are
+// passed through here after tcgen05.wait::ld, so that no use of them can be
+// scheduled above the wait.
+__device__ __forceinline__ void tmem_reg_fence16(uint32_t* r) {
+  asm volatile(""
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
+template <bool B>
+struct BoolTag {
+  static constexpr bool value = B;
+};
+
 // Matrix descriptor: no swizzle; addresses and offsets in 16-byte units.
 // lbo: byte distance between core matrices along K; sbo: along M / N.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
