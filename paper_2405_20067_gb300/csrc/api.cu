@@ -59,7 +59,7 @@ CommonLayout common_layout(const Sizes& z) {
   CommonLayout c;
   c.header = r.take(sizeof(WsHeader));
   c.loss = r.take(kLossParts * sizeof(double));  // fixed offset: ndg_loss_l2 knows no sizes
-  c.rec = r.take((size_t)z.Ge_cap * rec_floats(z.N) * sizeof(float));
+  c.rec = r.take((size_t)z.Ge_cap * rec_tc_floats(z.N) * sizeof(float));
   c.dflag = r.take((size_t)z.G_cap * sizeof(int));
   c.drank = r.take((size_t)z.G_cap * sizeof(int));
   c.dfresh = r.take((size_t)z.G_cap * sizeof(int));
@@ -390,6 +390,7 @@ ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q, const ndg_
   const int N = mix->N;
   PrepArgs pa = prep_args(mix);
   pa.rec = (float*)(w + c.rec);
+  pa.rec_kind = mode == NDG_MODE_TC ? 2 : 0;
   pa.status = &reinterpret_cast<WsHeader*>(w + c.header)->status;
   tr += launch_prep(N, pa, s);
   // Transpose the candidate lists to Gaussian-major order first (stable
@@ -420,7 +421,7 @@ ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q, const ndg_
   ba.part = (float*)(w + L.part);
   ba.status = pa.status;
   tr.begin();
-  tr += mode == NDG_MODE_TC ? launch_bwd_tc(N, ba, z.T, s) : launch_bwd(N, ba, z.T, s);
+  tr += mode == NDG_MODE_TC ? launch_bwd_h(N, ba, z.T, s) : launch_bwd(N, ba, z.T, s);
   tr.end();
   float* gsum = (float*)(w + L.gsum);
   tr += launch_segsum(ba.part, part_floats(N), goff, Ge, gsum, s);

@@ -1,0 +1,578 @@
+// bwd_h.cu -- the analytic backward (Section 3.3) on the tensor cores with
+// FP16 hi / lo operands (ndg_backward, NDG_MODE_TC, N <= 6).
+//
+// With the lifted form of the forward (s = phi(x~) . coef, e = 2^s, the
+// coefficients scaled by -log2(e) / 2 so that de/dQ = -e / 2 for the
+// quadratic form Q = (x~ - m~)^T A (x~ - m~)), every gradient of an entry
+// (Gaussian j, tile) is a sum over the tile's queries q of e_jq times a
+// query-side quantity:
+//   dl/dc_k = -1/2 sum_c w_jc sum_q e_jq dy_qc phi_qk      (lifted coefficients)
+//   dl/dw_jc = sum_q e_jq dy_qc                            (phi's constant entry)
+// so after  S^T = Coef Phi^T  (MMA 1, candidates on the TMEM lanes) and
+// E = 2^S, one more product  D2 = E Psi  with  Psi[q, (c, k)] = dy_qc phi_qk
+// (built once per tile) yields all of them (MMA 2, A = E read straight from
+// tensor memory, B = Psi from shared memory).  The entry's chain to
+// dl/dA (symmetric), dl/dm and dl/dM = 2 M dl/dA follows in registers, and
+// the record [dl/dM, dl/dm, dl/dw] goes to the entry's Gaussian-major slot,
+// as in the FP32 backward.
+//
+// Operands are FP16 pairs v = hi + lo (three products).  Range: features are
+// scaled per tile and dimension into [-1, 1] (the coefficients take the
+// inverse powers of two), dy is scaled per tile by a power of two into
+// [-1, 1], and coefficient rows above 2^14 are divided by a power of two that
+// the epilogue multiplies back before the exponential.
+//
+// CTA = one tile of up to 256 queries = up to two units of 128 queries,
+// 416 threads, one CTA per SM (all 512 TMEM columns):
+//   warps 0-3   builders: coefficient rows of a chunk of 128 candidates into
+//               one of CS stages (as in the forward), one arrival per warp;
+//   warp 12     MMA issuer (lane 0): MMA 1 of unit u + 1, then MMA 2 of unit u
+//               (TMEM: S / E buffers u & 1 at columns 128 (u & 1); D2 buffers
+//               i & 1 at 256 + NPSI (i & 1), accumulated over the chunk's units);
+//   warps 4-11  epilogue: warp w owns lanes 32 (w % 4) .. + 31 and columns
+//               64 ((w - 4) / 4) .. + 63 of each unit: e = 2^s written back in
+//               place as FP16 hi / lo (32 S columns -> 16 hi + 16 lo columns);
+//               warps of group (w - 4) / 4 also run the chain of every chunk i
+//               with i % 2 == group, one chunk behind.
+// Every wait is bounded; a timeout records NDG_ERR_TIMEOUT and the CTA lets
+// its issued MMAs finish (bounded) before it frees tensor memory.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "internal.h"
+#include "kernels.h"
+#include "tcgen05.cuh"
+
+namespace ndg {
+
+template <int N>
+struct BwdHShape {
+  static constexpr int P = tri(N);
+  static constexpr int F = P + N + 1;
+  static constexpr int KP = (F + 15) / 16 * 16;
+  static constexpr int NC = 128;            // candidates per chunk (MMA 1 M, TMEM lanes)
+  static constexpr int NPSI = 3 * KP;       // MMA 2 N: (colour, feature)
+  static constexpr int R = rec_floats(N);   // record head: A, m, w
+  static constexpr int R2 = rec_tc_floats(N);
+  static constexpr int RP = part_floats(N);
+  static constexpr int CS = 3;              // coefficient stages
+  static constexpr uint32_t SBO_K = (KP / 8) * 128;   // rows of KP FP16 values
+  static constexpr uint32_t SBO_Q = (256 / 8) * 128;  // Psi rows of 256 queries
+  static constexpr uint32_t PHI_BYTES = 256u * KP * 2;
+  static constexpr uint32_t HALF_BYTES = 128u * KP * 2;
+  static constexpr uint32_t PSI_BYTES = (uint32_t)NPSI * 256 * 2;
+  static constexpr uint32_t C_BYTES = (uint32_t)NC * KP * 2;
+  static constexpr uint32_t C_STAGE = 2 * C_BYTES + NC * 4;  // hi, lo, row factors
+  static constexpr uint32_t SMEM_USED = 2 * PHI_BYTES + 2 * PSI_BYTES + CS * C_STAGE + 128;
+  static constexpr uint32_t SMEM = SMEM_USED > 116u * 1024u ? SMEM_USED : 116u * 1024u;
+  static constexpr uint32_t TM_D2 = 256;
+  static_assert(256 + 2 * NPSI <= 512, "tensor memory");
+  static_assert(SMEM <= 227u * 1024u, "shared memory");
+  static_assert(NPSI % 16 == 0 && NPSI <= 256, "MMA 2 shape");
+};
+
+namespace {
+
+__device__ __forceinline__ void split_h2b(float v0, float v1, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(v0, v1);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(v0 - hf.x, v1 - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+__device__ __forceinline__ uint32_t koff(int row, int k, uint32_t sbo) {
+  return (uint32_t)(row >> 3) * sbo + (uint32_t)(k >> 3) * 128u + (uint32_t)(row & 7) * 16u +
+         (uint32_t)(k & 7) * 2u;
+}
+
+template <int KP>
+__device__ __forceinline__ void store_row_hb(uint8_t* hi, uint8_t* lo, int row, uint32_t sbo,
+                                             const float (&v)[KP]) {
+#pragma unroll
+  for (int k = 0; k < KP; k += 8) {
+    uint4 h, l;
+    split_h2b(v[k], v[k + 1], h.x, l.x);
+    split_h2b(v[k + 2], v[k + 3], h.y, l.y);
+    split_h2b(v[k + 4], v[k + 5], h.z, l.z);
+    split_h2b(v[k + 6], v[k + 7], h.w, l.w);
+    const uint32_t off = koff(row, k, sbo);
+    *reinterpret_cast<uint4*>(hi + off) = h;
+    *reinterpret_cast<uint4*>(lo + off) = l;
+  }
+}
+
+constexpr float kNegHalfLog2eB = -0.72134752044448170368f;
+constexpr float kRowMaxB = 16384.0f;
+
+}  // namespace
+
+template <int N>
+__global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
+  using S = BwdHShape<N>;
+  constexpr int P = S::P, F = S::F, KP = S::KP, NC = S::NC, NPSI = S::NPSI, CS = S::CS;
+  constexpr int R4 = S::R / 4, R2 = S::R2, RP = S::RP;
+  extern __shared__ __align__(128) uint8_t dsm[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)dsm + 127) & ~(uintptr_t)127);
+  uint8_t* PhiH = base;
+  uint8_t* PhiL = PhiH + S::PHI_BYTES;
+  uint8_t* PsiH = PhiL + S::PHI_BYTES;
+  uint8_t* PsiL = PsiH + S::PSI_BYTES;
+  uint8_t* Cst = PsiL + S::PSI_BYTES;  // CS stages of (hi, lo, row factors)
+  __shared__ uint64_t coef_full[CS], coef_empty[CS], s_full[2], e_full[2], d2_full[2], d2_empty[2],
+      drain;
+  __shared__ uint32_t tmem_base;
+  __shared__ float sred[8 * N * 2], sdy[8];
+  __shared__ float sctr[N], sh[N], s_dys;
+  __shared__ int s_abort;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long t = blockIdx.x;
+  const long long qt = t * a.tile;
+  const int nq = (int)(a.Q - qt < a.tile ? a.Q - qt : a.tile);
+  const int nh = nq > 128 ? 2 : 1;  // units (128-query blocks) per chunk
+
+  if (tid == 0) {
+    for (int i = 0; i < CS; ++i) {
+      mbar_init(&coef_full[i], 4);
+      mbar_init(&coef_empty[i], 1 + 8);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&s_full[i], 1);
+      mbar_init(&e_full[i], 8);
+      mbar_init(&d2_full[i], 1);
+      mbar_init(&d2_empty[i], 4);
+    }
+    mbar_init(&drain, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, 512);
+    tmem_relinquish();
+  }
+  // ---- per tile: centre, feature and dy scales, Phi rows and Psi columns
+  const bool is_epi = warp >= 4 && warp < 12;
+  const int row = tid - 128;
+  const bool active_row = is_epi && row < nq;
+  float xq[N], dq[3];
+#pragma unroll
+  for (int d = 0; d < N; ++d) xq[d] = active_row ? a.x[(qt + row) * N + d] : 0.0f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) dq[c] = active_row ? a.dy[(qt + row) * 3 + c] : 0.0f;
+  if (is_epi) {
+#pragma unroll
+    for (int d = 0; d < N; ++d) {
+      float lo = active_row ? xq[d] : INFINITY, hi = active_row ? xq[d] : -INFINITY;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      }
+      if (lane == 0) {
+        sred[((warp - 4) * N + d) * 2] = lo;
+        sred[((warp - 4) * N + d) * 2 + 1] = hi;
+      }
+    }
+    float m = fmaxf(fmaxf(fabsf(dq[0]), fabsf(dq[1])), fabsf(dq[2]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) sdy[warp - 4] = m;
+  }
+  __syncthreads();
+  if (tid < N) {
+    float lo = INFINITY, hi = -INFINITY;
+    for (int w = 0; w < 8; ++w) {
+      lo = fminf(lo, sred[(w * N + tid) * 2]);
+      hi = fmaxf(hi, sred[(w * N + tid) * 2 + 1]);
+    }
+    const float c = (lo <= hi) ? 0.5f * (lo + hi) : 0.0f;
+    sctr[tid] = c;
+    sh[tid] = (lo <= hi) ? pow2_ceil(fmaxf(hi - c, c - lo)) : 1.0f;
+  }
+  if (tid == N) {
+    float m = 0.0f;
+    for (int w = 0; w < 8; ++w) m = fmaxf(m, sdy[w]);
+    s_dys = pow2_ceil(m);
+  }
+  __syncthreads();
+  if (is_epi) {
+    float u[N];
+#pragma unroll
+    for (int d = 0; d < N; ++d) u[d] = active_row ? (xq[d] - sctr[d]) * (1.0f / sh[d]) : 0.0f;
+    float phi[KP];
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+      for (int j = 0; j <= i; ++j) phi[tri(i) + j] = u[i] * u[j];
+#pragma unroll
+    for (int i = 0; i < N; ++i) phi[P + i] = u[i];
+    phi[P + N] = active_row ? 1.0f : 0.0f;
+#pragma unroll
+    for (int k = F; k < KP; ++k) phi[k] = 0.0f;
+    store_row_hb<KP>(PhiH, PhiL, row, S::SBO_K, phi);
+    const float idys = 1.0f / s_dys;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float dc = dq[c] * idys;
+#pragma unroll
+      for (int k = 0; k < KP; k += 2) {
+        uint32_t hv, lv;
+        split_h2b(dc * phi[k], dc * phi[k + 1], hv, lv);
+        const int r = c * KP + k;  // rows r and r + 1, K index = query `row`
+        *reinterpret_cast<uint16_t*>(PsiH + koff(r, row, S::SBO_Q)) = (uint16_t)(hv & 0xffffu);
+        *reinterpret_cast<uint16_t*>(PsiH + koff(r + 1, row, S::SBO_Q)) = (uint16_t)(hv >> 16);
+        *reinterpret_cast<uint16_t*>(PsiL + koff(r, row, S::SBO_Q)) = (uint16_t)(lv & 0xffffu);
+        *reinterpret_cast<uint16_t*>(PsiL + koff(r + 1, row, S::SBO_Q)) = (uint16_t)(lv >> 16);
+      }
+    }
+  }
+  fence_proxy_async();
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  const long long beg = a.offsets[t], end = a.offsets[t + 1];
+  const int nchunks = (int)((end - beg + NC - 1) / NC);
+  const int U = nchunks * nh;
+  volatile int* abort_flag = &s_abort;
+  auto fail = [&]() {
+    atomicExch(&s_abort, 1);
+    if (a.status) set_status(a.status, NDG_ERR_TIMEOUT);
+  };
+
+  if (warp < 4) {
+    // ---- builders (thread j = candidate j of each chunk)
+    const int j = tid;
+    float hsc[N];
+#pragma unroll
+    for (int d = 0; d < N; ++d) hsc[d] = sh[d];
+    auto cand = [&](int i) -> int {
+      const long long c = beg + (long long)i * NC + j;
+      const int g = (i < nchunks && c < end) ? a.ids[c] : -1;
+      return ((unsigned)g < (unsigned)a.Ge) ? g : -1;
+    };
+    auto load = [&](int g, float4 (&r)[R4]) {
+      if (g >= 0) {
+        const float4* src = reinterpret_cast<const float4*>(a.rec + (size_t)g * R2);
+#pragma unroll
+        for (int k = 0; k < R4; ++k) r[k] = __ldg(src + k);
+      } else {
+#pragma unroll
+        for (int k = 0; k < R4; ++k) r[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    };
+    float4 cur[R4], nxt[R4];
+    load(cand(0), cur);
+    int g_next = cand(1);
+    for (int i = 0; i < nchunks; ++i) {
+      const int s = i % CS;
+      load(g_next, nxt);
+      g_next = cand(i + 2);
+      bool ok = true;
+      if (i >= CS) ok = warp_wait(&coef_empty[s], ((i / CS) - 1) & 1, abort_flag);
+      if (!ok && lane == 0) fail();
+      uint8_t* st = Cst + s * S::C_STAGE;
+      if (ok) {
+        float buf[S::R];
+#pragma unroll
+        for (int k = 0; k < R4; ++k) {
+          buf[4 * k] = cur[k].x; buf[4 * k + 1] = cur[k].y;
+          buf[4 * k + 2] = cur[k].z; buf[4 * k + 3] = cur[k].w;
+        }
+        float coef[KP], mt[N];
+#pragma unroll
+        for (int d = 0; d < N; ++d) mt[d] = buf[P + d] - sctr[d];
+        float cst = 0.0f;
+#pragma unroll
+        for (int d = 0; d < N; ++d) {
+          float s2 = 0.0f;
+#pragma unroll
+          for (int k = 0; k < N; ++k) s2 = fmaf(buf[d >= k ? tri(d) + k : tri(k) + d], mt[k], s2);
+          coef[P + d] = (kNegHalfLog2eB * -2.0f) * s2 * hsc[d];
+          cst = fmaf(mt[d], s2, cst);
+        }
+#pragma unroll
+        for (int d = 0; d < N; ++d)
+#pragma unroll
+          for (int k = 0; k <= d; ++k)
+            coef[tri(d) + k] = kNegHalfLog2eB * (d == k ? buf[tri(d) + k] : 2.0f * buf[tri(d) + k]) *
+                               (hsc[d] * hsc[k]);
+        coef[P + N] = kNegHalfLog2eB * cst;
+#pragma unroll
+        for (int k = F; k < KP; ++k) coef[k] = 0.0f;
+        float mx = 0.0f;
+#pragma unroll
+        for (int k = 0; k < F; ++k) mx = fmaxf(mx, fabsf(coef[k]));
+        float back = 1.0f;
+        if (mx > kRowMaxB) {
+          int e = (int)((__float_as_uint(mx) >> 23) & 0xffu) - 127 - 13;
+          e = e > 120 ? 120 : e;
+          const float down = __uint_as_float((uint32_t)(127 - e) << 23);
+          back = __uint_as_float((uint32_t)(127 + e) << 23);
+#pragma unroll
+          for (int k = 0; k < KP; ++k) coef[k] *= down;
+        }
+        store_row_hb<KP>(st, st + S::C_BYTES, j, S::SBO_K, coef);
+        reinterpret_cast<float*>(st + 2 * S::C_BYTES)[j] = back;
+      }
+      fence_proxy_async();
+      warp_arrive(&coef_full[s]);
+#pragma unroll
+      for (int k = 0; k < R4; ++k) cur[k] = nxt[k];
+      if (__shfl_sync(0xffffffffu, (!ok || *abort_flag) ? 1 : 0, 0)) break;
+    }
+  } else if (warp == 12) {
+    // ---- MMA issuer
+    if (lane == 0 && U > 0) {
+      constexpr uint32_t IDESC1 = idesc_f16(128);
+      constexpr uint32_t IDESC2 = idesc_f16(NPSI);
+      const uint32_t phh = smem_u32(PhiH), phl = smem_u32(PhiL);
+      const uint32_t psh = smem_u32(PsiH), psl = smem_u32(PsiL);
+      auto mma1 = [&](int u) -> bool {
+        const int i = u / nh, h = u - i * nh, s = i % CS, sb = u & 1;
+        if (h == 0 && !mbar_wait_sleep(&coef_full[s], (i / CS) & 1, abort_flag)) return false;
+        fence_after_sync();
+        uint8_t* st = Cst + s * S::C_STAGE;
+        const uint32_t ch = smem_u32(st), cl = smem_u32(st + S::C_BYTES);
+        const uint32_t ho = (uint32_t)h * S::HALF_BYTES;
+        const uint32_t d = tmem + (uint32_t)(sb * 128);
+#pragma unroll
+        for (int ks = 0; ks < KP / 16; ++ks) {
+          const uint32_t ko = (uint32_t)ks * 256u;
+          const uint64_t dch = smem_desc(ch + ko, 128, S::SBO_K);
+          const uint64_t dcl = smem_desc(cl + ko, 128, S::SBO_K);
+          const uint64_t dph = smem_desc(phh + ho + ko, 128, S::SBO_K);
+          const uint64_t dpl = smem_desc(phl + ho + ko, 128, S::SBO_K);
+          mma_f16(d, dch, dph, IDESC1, ks > 0 ? 1u : 0u);
+          mma_f16(d, dch, dpl, IDESC1, 1u);
+          mma_f16(d, dcl, dph, IDESC1, 1u);
+        }
+        mma_commit(&s_full[sb]);
+        if (h == nh - 1) mma_commit(&coef_empty[s]);
+        return true;
+      };
+      auto mma2 = [&](int u) -> bool {
+        const int i = u / nh, h = u - i * nh, sb = u & 1, db = i & 1;
+        if (!mbar_wait_sleep(&e_full[sb], (u >> 1) & 1, abort_flag)) return false;
+        if (h == 0 && i >= 2 && !mbar_wait_sleep(&d2_empty[db], ((i >> 1) - 1) & 1, abort_flag))
+          return false;
+        fence_after_sync();
+        const uint32_t d = tmem + S::TM_D2 + (uint32_t)(db * NPSI);
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {  // 16 queries per K step
+          const uint32_t eh = tmem + (uint32_t)(sb * 128 + 32 * (kk >> 1) + 8 * (kk & 1));
+          const uint32_t el = eh + 16u;
+          const uint32_t qo = (uint32_t)(16 * h + 2 * kk) * 128u;
+          const uint64_t dsh = smem_desc(psh + qo, 128, S::SBO_Q);
+          const uint64_t dsl = smem_desc(psl + qo, 128, S::SBO_Q);
+          mma_f16_ts(d, eh, dsh, IDESC2, (h > 0 || kk > 0) ? 1u : 0u);
+          mma_f16_ts(d, eh, dsl, IDESC2, 1u);
+          mma_f16_ts(d, el, dsh, IDESC2, 1u);
+        }
+        if (h == nh - 1) mma_commit(&d2_full[db]);
+        return true;
+      };
+      bool ok = mma1(0);
+      for (int u = 0; ok && u < U; ++u) {
+        if (u + 1 < U) ok = mma1(u + 1);
+        if (ok) ok = mma2(u);
+      }
+      if (!ok) fail();
+    }
+  } else {
+    // ---- epilogue and chain
+    const int quad = warp & 3, grp = (warp - 4) >> 2;
+    const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+    const int j = quad * 32 + lane;  // candidate lane
+    auto chain = [&](int ic) -> bool {
+      const int db = ic & 1;
+      if (!warp_wait(&d2_full[db], (ic >> 1) & 1, abort_flag)) return false;
+      fence_after_sync();
+      const long long c0 = beg + (long long)ic * NC;
+      const long long e = c0 + j;
+      const int g = e < end ? a.ids[e] : -1;
+      const bool live = (unsigned)g < (unsigned)a.Ge;
+      float hd[S::R];
+      {
+        const float4* src = reinterpret_cast<const float4*>(a.rec + (size_t)(live ? g : 0) * R2);
+#pragma unroll
+        for (int k = 0; k < R4; ++k) {
+          const float4 v = live ? __ldg(src + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+          hd[4 * k] = v.x; hd[4 * k + 1] = v.y; hd[4 * k + 2] = v.z; hd[4 * k + 3] = v.w;
+        }
+      }
+      // Gc_k = sum_c w_c D2[c][k], dl/dw_c = D2[c][P + N]
+      float Gc[F], gw[3];
+#pragma unroll
+      for (int k = 0; k < F; ++k) Gc[k] = 0.0f;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        uint32_t v[KP];
+#pragma unroll
+        for (int cb = 0; cb < KP; cb += 16)
+          tmem_ld16_nowait(tmem + lane_off + S::TM_D2 + (uint32_t)(db * NPSI + c * KP + cb), v + cb);
+        tmem_wait_ld();
+#pragma unroll
+        for (int cb = 0; cb < KP; cb += 16) tmem_reg_fence16(v + cb);
+        const float wc = hd[P + N + c];
+#pragma unroll
+        for (int k = 0; k < F; ++k) Gc[k] = fmaf(wc, __uint_as_float(v[k]), Gc[k]);
+        gw[c] = __uint_as_float(v[P + N]);
+      }
+      fence_before_sync();
+      warp_arrive(&d2_empty[db]);
+      if (!live) return true;
+      // back to the unscaled features and dy (Psi held dy / dys):
+      // Gc = -1/2 h_k dys sum_c w_c D2
+      const float gsc = -0.5f * s_dys;
+      float hsc[N];
+#pragma unroll
+      for (int d = 0; d < N; ++d) hsc[d] = sh[d];
+#pragma unroll
+      for (int d = 0; d < N; ++d)
+#pragma unroll
+        for (int k = 0; k <= d; ++k) Gc[tri(d) + k] *= gsc * (hsc[d] * hsc[k]);
+#pragma unroll
+      for (int d = 0; d < N; ++d) Gc[P + d] *= gsc * hsc[d];
+      Gc[P + N] *= gsc;
+      float mt[N];
+#pragma unroll
+      for (int d = 0; d < N; ++d) mt[d] = hd[P + d] - sctr[d];
+      const float Gc0 = Gc[P + N];
+      float rec[RP];
+      // dl/dm = dl/dm~ = 2 A (Gc0 m~ - G_lin)
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        float s2 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+          s2 = fmaf(hd[i >= k ? tri(i) + k : tri(k) + i], Gc0 * mt[k] - Gc[P + k], s2);
+        rec[P + i] = 2.0f * s2;
+      }
+      // symmetric gradient with respect to A (all matrix entries)
+      float Gf[N][N];
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int k = 0; k <= i; ++k) {
+          float gv;
+          if (i == k)
+            gv = Gc[tri(i) + i] - 2.0f * Gc[P + i] * mt[i] + Gc0 * mt[i] * mt[i];
+          else
+            gv = Gc[tri(i) + k] - (Gc[P + i] * mt[k] + Gc[P + k] * mt[i]) + Gc0 * mt[i] * mt[k];
+          Gf[i][k] = gv;
+          Gf[k][i] = gv;
+        }
+      // dl/dM = 2 M G (lower part), M from the record tail
+      float M[P];
+      {
+        const float* src = a.rec + (size_t)g * R2 + S::R;
+#pragma unroll
+        for (int k = 0; k < P; ++k) M[k] = __ldg(src + k);
+      }
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int k = 0; k <= i; ++k) {
+          float s2 = 0.0f;
+#pragma unroll
+          for (int l = 0; l <= i; ++l) s2 = fmaf(M[tri(i) + l], Gf[l][k], s2);
+          rec[tri(i) + k] = 2.0f * s2;
+        }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) rec[P + N + c] = gw[c] * s_dys;
+#pragma unroll
+      for (int k = P + N + 3; k < RP; ++k) rec[k] = 0.0f;
+      const long long slot = a.slot ? (long long)a.slot[e] : e;
+      float* out = a.part + (size_t)slot * RP;
+#pragma unroll
+      for (int k = 0; k < RP; k += 4)
+        *reinterpret_cast<float4*>(out + k) = make_float4(rec[k], rec[k + 1], rec[k + 2], rec[k + 3]);
+      return true;
+    };
+
+    float back = 1.0f;
+    bool ok = true;
+    for (int u = 0; u < U; ++u) {
+      const int i = u / nh, h = u - i * nh, s = i % CS, sb = u & 1;
+      ok = warp_wait(&s_full[sb], (u >> 1) & 1, abort_flag);
+      if (ok && h == 0) ok = warp_wait(&coef_full[s], (i / CS) & 1, abort_flag);
+      if (!ok) break;
+      fence_after_sync();
+      if (h == 0) {
+        back = reinterpret_cast<const float*>(Cst + s * S::C_STAGE + 2 * S::C_BYTES)[j];
+        warp_arrive(&coef_empty[s]);
+      }
+#pragma unroll 1
+      for (int cb = 0; cb < 64; cb += 32) {
+        const uint32_t col = tmem + lane_off + (uint32_t)(sb * 128 + grp * 64 + cb);
+        uint32_t v[32];
+        tmem_ld16_nowait(col, v);
+        tmem_ld16_nowait(col + 16u, v + 16);
+        tmem_wait_ld();
+        tmem_reg_fence16(v);
+        tmem_reg_fence16(v + 16);
+        uint32_t hi[16], lo[16];
+#pragma unroll
+        for (int p = 0; p < 16; ++p) {
+          const float2 sv = __fmul2_rn(make_float2(__uint_as_float(v[2 * p]), __uint_as_float(v[2 * p + 1])),
+                                       make_float2(back, back));
+          split_h2b(ex2_approx(sv.x), ex2_approx(sv.y), hi[p], lo[p]);
+        }
+        tmem_st16(col, hi);
+        tmem_st16(col + 16u, lo);
+      }
+      tmem_wait_st();
+      fence_before_sync();
+      warp_arrive(&e_full[sb]);
+      if (h == nh - 1 && i >= 1 && ((i - 1) & 1) == grp) {
+        ok = chain(i - 1);
+        if (!ok) break;
+      }
+      if (__shfl_sync(0xffffffffu, *abort_flag ? 1 : 0, 0)) {
+        ok = false;
+        break;
+      }
+    }
+    if (ok && nchunks >= 1 && ((nchunks - 1) & 1) == grp) ok = chain(nchunks - 1);
+    if (!ok && lane == 0) fail();
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 12 && lane == 0) {
+    // every MMA this thread issued has completed once this commit arrives
+    mma_commit(&drain);
+    if (!mbar_wait_bounded(&drain, 0, kWaitLimit)) fail();
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after_sync();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+int launch_bwd_h(int N, const BwdArgs& a, long long T, cudaStream_t s) {
+  if (T <= 0) return 0;
+#define L_BH(n)                                                                         \
+  {                                                                                     \
+    cudaFuncSetAttribute(bwd_h_kernel<n>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                         (int)BwdHShape<n>::SMEM);                                      \
+    bwd_h_kernel<n><<<(unsigned)T, 416, BwdHShape<n>::SMEM, s>>>(a);                    \
+  }
+  switch (N) {
+    case 1: L_BH(1); break;
+    case 2: L_BH(2); break;
+    case 3: L_BH(3); break;
+    case 4: L_BH(4); break;
+    case 5: L_BH(5); break;
+    case 6: L_BH(6); break;
+    default: return 0;
+  }
+#undef L_BH
+  return 1;
+}
+
+}  // namespace ndg

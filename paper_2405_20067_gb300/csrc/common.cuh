@@ -11,6 +11,9 @@ __host__ __device__ constexpr int tri(int n) { return n * (n + 1) / 2; }
 // Prepared record per evaluated Gaussian: M = L^{-1} packed lower (P), m (N),
 // w (3), padded to a multiple of 4 floats (16-byte rows).
 __host__ __device__ constexpr int rec_floats(int n) { return (tri(n) + n + 3 + 3) / 4 * 4; }
+// Record of the tensor-core backward: the head as above with A = M^T M in
+// place of M, followed by M itself (padded to a multiple of 4 floats).
+__host__ __device__ constexpr int rec_tc_floats(int n) { return rec_floats(n) + (tri(n) + 3) / 4 * 4; }
 // Backward partial record: sum beta z d^T (P), sum beta z (N), sum dy e (3).
 __host__ __device__ constexpr int part_floats(int n) { return (tri(n) + n + 3 + 3) / 4 * 4; }
 __host__ __device__ constexpr int key_pad(int k) { return k <= 0 ? 0 : (k + 7) / 8 * 8; }

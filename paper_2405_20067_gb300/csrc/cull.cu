@@ -199,9 +199,9 @@ __global__ void __launch_bounds__(128) prep_kernel(PrepArgs a) {
         M[tri(i) + j] = -s / L[tri(i) + i];
       }
     }
-    float* out = a.rec + (size_t)e * R;
+    float* out = a.rec + (size_t)e * (a.rec_kind == 2 ? rec_tc_floats(N) : R);
     float buf[R];
-    if (a.rec_kind == 1) {
+    if (a.rec_kind >= 1) {
       // A = V^-1 = M^T M (lower, packed): A_ij = sum_{k >= i} M_ki M_kj, j <= i
 #pragma unroll
       for (int i = 0; i < N; ++i)
@@ -225,6 +225,15 @@ __global__ void __launch_bounds__(128) prep_kernel(PrepArgs a) {
 #pragma unroll
     for (int i = 0; i < R; i += 4)
       *reinterpret_cast<float4*>(out + i) = make_float4(buf[i], buf[i + 1], buf[i + 2], buf[i + 3]);
+    if (a.rec_kind == 2) {
+      constexpr int PM = (P + 3) / 4 * 4;
+      float mb[PM];
+#pragma unroll
+      for (int i = 0; i < PM; ++i) mb[i] = i < P ? (float)M[i] : 0.0f;
+#pragma unroll
+      for (int i = 0; i < PM; i += 4)
+        *reinterpret_cast<float4*>(out + R + i) = make_float4(mb[i], mb[i + 1], mb[i + 2], mb[i + 3]);
+    }
   }
 
   if (a.gkey || a.bin) {

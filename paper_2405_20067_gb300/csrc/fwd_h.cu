@@ -22,10 +22,12 @@
 //   warps 0-3   builders: thread j turns candidate j of a chunk of 128 into
 //               its coefficient row (FP16 hi / lo, K-major no-swizzle layout)
 //               and weight pair entry in one of CS shared-memory stages; the
-//               records of the next chunk are loaded into registers meanwhile.
-//               After a named barrier thread 0 issues the chunk's MMAs into
-//               accumulator buffer i & 1 and commits them to acc_full and
-//               coef_empty;
+//               records of the next chunk are loaded into registers meanwhile;
+//               each warp then arrives on coef_full.  The warps are coupled
+//               only through these barriers, so warps 0-2 may run ahead;
+//               lane 0 of warp 3 issues the MMAs of a chunk once its stage is
+//               full and accumulator buffer i & 1 is free, and commits them
+//               to acc_full and coef_empty;
 //   warps 4-11  epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of both
 //               row blocks (query rows r and r + 128), columns 64 ((w - 4) / 4)
 //               .. + 63 (half of the candidates), with the 16x256b load shape
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
   };
 
   if (warp < 4) {
-    // ---- builders; thread 0 also issues the MMAs
+    // ---- builders
     const int j = tid;
     float hsc[N];
 #pragma unroll
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
     const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo);
     constexpr uint32_t IDESC = idesc_f16(NC);
     for (int i = 0; i < nchunks; ++i) {
-      const int s = i % CS, b = i & 1;
+      const int s = i % CS;
       load(g_next, nxt);  // chunk i + 1 (zeros past the end)
       g_next = cand(i + 2);
       bool ok = true;
@@ -299,10 +301,15 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
       warp_arrive(&coef_full[s]);
 #pragma unroll
       for (int k = 0; k < R4; ++k) cur[k] = nxt[k];
-      // every builder takes the same branch
-      if (bar_red_or(1, 128, !ok || *abort_flag)) break;
-      if (tid == 0) {
-        if (i >= 2 && !mbar_wait_sleep(&acc_empty[b], ((i >> 1) - 1) & 1, abort_flag)) {
+      // one decision per warp
+      if (__shfl_sync(0xffffffffu, (!ok || *abort_flag) ? 1 : 0, 0)) break;
+      if (warp == 3 && lane == 0) {
+        // MMA issue for chunk i: once all four builder warps have filled the
+        // stage and accumulator buffer i & 1 is free
+        const int b = i & 1;
+        bool ok2 = mbar_wait_sleep(&coef_full[s], (i / CS) & 1, abort_flag);
+        if (ok2 && i >= 2) ok2 = mbar_wait_sleep(&acc_empty[b], ((i >> 1) - 1) & 1, abort_flag);
+        if (!ok2) {
           fail();
         } else {
           fence_after_sync();
@@ -326,6 +333,7 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
           mma_commit(&coef_empty[s]);
         }
       }
+      __syncwarp();
     }
   } else {
     // ---- epilogue (tcgen05.ld 16x256b: thread t holds lanes t/4 and t/4 + 8
@@ -441,7 +449,7 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
   }
   fence_before_sync();
   __syncthreads();
-  if (tid == 0) {
+  if (warp == 3 && lane == 0) {
     // every MMA this thread issued has completed once this commit arrives
     mma_commit(&drain);
     if (!mbar_wait_bounded(&drain, 0, kWaitLimit)) fail();

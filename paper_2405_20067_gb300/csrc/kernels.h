@@ -11,7 +11,8 @@ struct PrepArgs {
   const float *mean, *theta, *alpha_raw, *color_raw;
   const float *u_theta, *m_u, *c_alpha_raw, *c_color_raw;
   float* rec;  // [Ge][rec_floats(N)] or null
-  int rec_kind;  // 0: M = L^-1 packed; 1: A = M^T M packed (lifted tensor-core form)
+  int rec_kind;  // 0: M = L^-1 packed; 1: A = M^T M packed (lifted tensor-core form);
+                 // 2: kind 1 followed by M (tensor-core backward; stride rec_tc_floats)
   // cull keys (when gkey or bin is set)
   int k, KP, B;
   const float* proj;
@@ -112,6 +113,7 @@ int launch_fwd(int N, const FwdArgs& a, long long T, cudaStream_t s);
 int launch_fwd_tc(int N, const FwdArgs& a, long long T, cudaStream_t s);
 int launch_fwd_h(int N, const FwdArgs& a, long long T, cudaStream_t s);  // N <= 8
 int launch_bwd_tc(int N, const BwdArgs& a, long long T, cudaStream_t s);  // N <= 6
+int launch_bwd_h(int N, const BwdArgs& a, long long T, cudaStream_t s);   // N <= 6
 size_t fwd_tc_smem(int N);
 int launch_loss(const float* y, const float* target, float* dy, long long n, double* part,
                  double* loss, cudaStream_t s);
