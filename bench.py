@@ -355,7 +355,7 @@ def main():
     ap.add_argument("--no-render", action="store_true", help="skip the N=10 1080p render metric")
     ap.add_argument("--no-fp32-form", action="store_true",
                     help="skip timing the plain FP32 form next to the chosen form")
-    ap.add_argument("--bwd-form", default="fp32", choices=["fp32", "tc"],
+    ap.add_argument("--bwd-form", default="tc", choices=["fp32", "tc"],
                     help="backward of the chosen form (its forward is the tensor-core one)")
     ap.add_argument("--workload", default="fit_n6", choices=sorted(WORKLOADS),
                     help="fit_n6: the headline workload; small_n6: 1/8 of it for profiling")

@@ -429,6 +429,7 @@ ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q, const ndg_
   ch.G = mix->G;
   ch.has_children = mix->has_children;
   ch.gsum = gsum;
+  ch.part_kind = mode == NDG_MODE_TC ? 1 : 0;
   ch.theta = mix->theta;
   ch.alpha_raw = mix->alpha_raw;
   ch.color_raw = mix->color_raw;

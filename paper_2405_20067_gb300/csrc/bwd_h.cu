@@ -11,10 +11,11 @@
 // so after  S^T = Coef Phi^T  (MMA 1, candidates on the TMEM lanes) and
 // E = 2^S, one more product  D2 = E Psi  with  Psi[q, (c, k)] = dy_qc phi_qk
 // (built once per tile) yields all of them (MMA 2, A = E read straight from
-// tensor memory, B = Psi from shared memory).  The entry's chain to
-// dl/dA (symmetric), dl/dm and dl/dM = 2 M dl/dA follows in registers, and
-// the record [dl/dM, dl/dm, dl/dw] goes to the entry's Gaussian-major slot,
-// as in the FP32 backward.
+// tensor memory, B = Psi from shared memory).  Per entry the kernel then
+// forms the frame-free record [G = dl/dA (symmetric), v = Gc0 m~ - G_lin,
+// dl/dw] at the entry's Gaussian-major slot; both remaining factors are
+// linear with per-Gaussian matrices, dl/dM = 2 M sum G and dl/dm = 2 A sum v,
+// and are applied once per Gaussian after the segmented sum.
 //
 // Operands are FP16 pairs v = hi + lo (three products).  Range: features are
 // scaled per tile and dimension into [-1, 1] (the coefficients take the
@@ -63,13 +64,15 @@ struct BwdHShape {
   static constexpr uint32_t HALF_BYTES = 128u * KP * 2;
   static constexpr uint32_t PSI_BYTES = (uint32_t)NPSI * 256 * 2;
   static constexpr uint32_t C_BYTES = (uint32_t)NC * KP * 2;
-  static constexpr uint32_t C_STAGE = 2 * C_BYTES + NC * 4;  // hi, lo, row factors
+  static constexpr uint32_t STASH = 48;  // per candidate: m~ (N), w (3), slot, pad
+  static constexpr uint32_t C_STAGE = 2 * C_BYTES + NC * 4 + NC * STASH;  // hi, lo, row factors, stash
   static constexpr uint32_t SMEM_USED = 2 * PHI_BYTES + 2 * PSI_BYTES + CS * C_STAGE + 128;
   static constexpr uint32_t SMEM = SMEM_USED > 116u * 1024u ? SMEM_USED : 116u * 1024u;
   static constexpr uint32_t TM_D2 = 256;
   static_assert(256 + 2 * NPSI <= 512, "tensor memory");
   static_assert(SMEM <= 227u * 1024u, "shared memory");
   static_assert(NPSI % 16 == 0 && NPSI <= 256, "MMA 2 shape");
+  static_assert(N + 4 <= 12, "stash");
 };
 
 namespace {
@@ -136,7 +139,7 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
   if (tid == 0) {
     for (int i = 0; i < CS; ++i) {
       mbar_init(&coef_full[i], 4);
-      mbar_init(&coef_empty[i], 1 + 8);
+      mbar_init(&coef_empty[i], 1 + 8 + 4);  // MMA 1, epilogue warps, chain warps
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&s_full[i], 1);
@@ -243,15 +246,20 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
   };
 
   if (warp < 4) {
-    // ---- builders (thread j = candidate j of each chunk)
+    // ---- builders (thread j = candidate j of each chunk); the records of
+    // chunk i + 1 are loaded into registers while chunk i is built
     const int j = tid;
     float hsc[N];
 #pragma unroll
     for (int d = 0; d < N; ++d) hsc[d] = sh[d];
-    auto cand = [&](int i) -> int {
-      const long long c = beg + (long long)i * NC + j;
-      const int g = (i < nchunks && c < end) ? a.ids[c] : -1;
-      return ((unsigned)g < (unsigned)a.Ge) ? g : -1;
+    // candidate j of chunk i: Gaussian index (or -1) and output slot
+    auto cand = [&](int i) -> int2 {
+      const long long e = beg + (long long)i * NC + j;
+      const bool in = i < nchunks && e < end;
+      const int g = in ? a.ids[e] : -1;
+      const bool live = (unsigned)g < (unsigned)a.Ge;
+      const int sl = live ? (a.slot ? a.slot[e] : (int)e) : -1;
+      return make_int2(live ? g : -1, sl);
     };
     auto load = [&](int g, float4 (&r)[R4]) {
       if (g >= 0) {
@@ -263,91 +271,114 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
         for (int k = 0; k < R4; ++k) r[k] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     };
-    float4 cur[R4], nxt[R4];
-    load(cand(0), cur);
-    int g_next = cand(1);
-    for (int i = 0; i < nchunks; ++i) {
+    auto build = [&](int i, const float4 (&cur)[R4], int slot) -> bool {
       const int s = i % CS;
-      load(g_next, nxt);
-      g_next = cand(i + 2);
-      bool ok = true;
-      if (i >= CS) ok = warp_wait(&coef_empty[s], ((i / CS) - 1) & 1, abort_flag);
-      if (!ok && lane == 0) fail();
+      float buf[S::R];
+#pragma unroll
+      for (int k = 0; k < R4; ++k) {
+        buf[4 * k] = cur[k].x; buf[4 * k + 1] = cur[k].y;
+        buf[4 * k + 2] = cur[k].z; buf[4 * k + 3] = cur[k].w;
+      }
+      if (i >= CS && !warp_wait(&coef_empty[s], ((i / CS) - 1) & 1, abort_flag)) return false;
       uint8_t* st = Cst + s * S::C_STAGE;
-      if (ok) {
-        float buf[S::R];
+      float coef[KP], mt[N];
 #pragma unroll
-        for (int k = 0; k < R4; ++k) {
-          buf[4 * k] = cur[k].x; buf[4 * k + 1] = cur[k].y;
-          buf[4 * k + 2] = cur[k].z; buf[4 * k + 3] = cur[k].w;
-        }
-        float coef[KP], mt[N];
+      for (int d = 0; d < N; ++d) mt[d] = buf[P + d] - sctr[d];
+      float cst = 0.0f;
 #pragma unroll
-        for (int d = 0; d < N; ++d) mt[d] = buf[P + d] - sctr[d];
-        float cst = 0.0f;
+      for (int d = 0; d < N; ++d) {
+        float s2 = 0.0f;
 #pragma unroll
-        for (int d = 0; d < N; ++d) {
-          float s2 = 0.0f;
+        for (int k = 0; k < N; ++k) s2 = fmaf(buf[d >= k ? tri(d) + k : tri(k) + d], mt[k], s2);
+        coef[P + d] = (kNegHalfLog2eB * -2.0f) * s2 * hsc[d];
+        cst = fmaf(mt[d], s2, cst);
+      }
 #pragma unroll
-          for (int k = 0; k < N; ++k) s2 = fmaf(buf[d >= k ? tri(d) + k : tri(k) + d], mt[k], s2);
-          coef[P + d] = (kNegHalfLog2eB * -2.0f) * s2 * hsc[d];
-          cst = fmaf(mt[d], s2, cst);
-        }
+      for (int d = 0; d < N; ++d)
 #pragma unroll
-        for (int d = 0; d < N; ++d)
+        for (int k = 0; k <= d; ++k)
+          coef[tri(d) + k] = kNegHalfLog2eB * (d == k ? buf[tri(d) + k] : 2.0f * buf[tri(d) + k]) *
+                             (hsc[d] * hsc[k]);
+      coef[P + N] = kNegHalfLog2eB * cst;
 #pragma unroll
-          for (int k = 0; k <= d; ++k)
-            coef[tri(d) + k] = kNegHalfLog2eB * (d == k ? buf[tri(d) + k] : 2.0f * buf[tri(d) + k]) *
-                               (hsc[d] * hsc[k]);
-        coef[P + N] = kNegHalfLog2eB * cst;
+      for (int k = F; k < KP; ++k) coef[k] = 0.0f;
+      float mx = 0.0f;
 #pragma unroll
-        for (int k = F; k < KP; ++k) coef[k] = 0.0f;
-        float mx = 0.0f;
+      for (int k = 0; k < F; ++k) mx = fmaxf(mx, fabsf(coef[k]));
+      float back = 1.0f;
+      if (mx > kRowMaxB) {
+        int ex = (int)((__float_as_uint(mx) >> 23) & 0xffu) - 127 - 13;
+        ex = ex > 120 ? 120 : ex;
+        const float down = __uint_as_float((uint32_t)(127 - ex) << 23);
+        back = __uint_as_float((uint32_t)(127 + ex) << 23);
 #pragma unroll
-        for (int k = 0; k < F; ++k) mx = fmaxf(mx, fabsf(coef[k]));
-        float back = 1.0f;
-        if (mx > kRowMaxB) {
-          int e = (int)((__float_as_uint(mx) >> 23) & 0xffu) - 127 - 13;
-          e = e > 120 ? 120 : e;
-          const float down = __uint_as_float((uint32_t)(127 - e) << 23);
-          back = __uint_as_float((uint32_t)(127 + e) << 23);
+        for (int k = 0; k < KP; ++k) coef[k] *= down;
+      }
+      store_row_hb<KP>(st, st + S::C_BYTES, j, S::SBO_K, coef);
+      reinterpret_cast<float*>(st + 2 * S::C_BYTES)[j] = back;
+      {
+        // what the chain of this entry needs: m~, w and the output slot
+        float sv[12];
 #pragma unroll
-          for (int k = 0; k < KP; ++k) coef[k] *= down;
-        }
-        store_row_hb<KP>(st, st + S::C_BYTES, j, S::SBO_K, coef);
-        reinterpret_cast<float*>(st + 2 * S::C_BYTES)[j] = back;
+        for (int d = 0; d < N; ++d) sv[d] = mt[d];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sv[N + c] = buf[P + N + c];
+        sv[N + 3] = __int_as_float(slot);
+#pragma unroll
+        for (int k = N + 4; k < 12; ++k) sv[k] = 0.0f;
+        float4* dst = reinterpret_cast<float4*>(st + 2 * S::C_BYTES + NC * 4 + (uint32_t)j * S::STASH);
+        dst[0] = make_float4(sv[0], sv[1], sv[2], sv[3]);
+        dst[1] = make_float4(sv[4], sv[5], sv[6], sv[7]);
+        dst[2] = make_float4(sv[8], sv[9], sv[10], sv[11]);
       }
       fence_proxy_async();
       warp_arrive(&coef_full[s]);
+      return true;
+    };
+    float4 cur[R4], nxt[R4];
+    const int2 c0i = cand(0);
+    load(c0i.x, cur);
+    int slot_cur = c0i.y;
+    int2 c_next = cand(1);
+    bool ok = true;
+    for (int i = 0; i < nchunks; ++i) {
+      load(c_next.x, nxt);
+      const int slot_nxt = c_next.y;
+      c_next = cand(i + 2);
+      ok = build(i, cur, slot_cur);
+      slot_cur = slot_nxt;
 #pragma unroll
       for (int k = 0; k < R4; ++k) cur[k] = nxt[k];
-      if (__shfl_sync(0xffffffffu, (!ok || *abort_flag) ? 1 : 0, 0)) break;
+      if (__shfl_sync(0xffffffffu, (!ok || *abort_flag) ? 1 : 0, 0)) {
+        ok = false;
+        break;
+      }
     }
+    if (!ok && lane == 0) fail();
   } else if (warp == 12) {
     // ---- MMA issuer
     if (lane == 0 && U > 0) {
       constexpr uint32_t IDESC1 = idesc_f16(128);
       constexpr uint32_t IDESC2 = idesc_f16(NPSI);
-      const uint32_t phh = smem_u32(PhiH), phl = smem_u32(PhiL);
-      const uint32_t psh = smem_u32(PsiH), psl = smem_u32(PsiL);
+      // descriptor bases (a descriptor for base + off is base + off / 16)
+      const uint64_t dPhi = smem_desc(smem_u32(PhiH), 128, S::SBO_K);
+      const uint64_t dPsi = smem_desc(smem_u32(PsiH), 128, S::SBO_Q);
+      const uint64_t dC0 = smem_desc(smem_u32(Cst), 128, S::SBO_K);
+      constexpr uint64_t PHI_LO = S::PHI_BYTES >> 4, PSI_LO = S::PSI_BYTES >> 4;
+      constexpr uint64_t C_LO = S::C_BYTES >> 4;
       auto mma1 = [&](int u) -> bool {
         const int i = u / nh, h = u - i * nh, s = i % CS, sb = u & 1;
         if (h == 0 && !mbar_wait_sleep(&coef_full[s], (i / CS) & 1, abort_flag)) return false;
         fence_after_sync();
-        uint8_t* st = Cst + s * S::C_STAGE;
-        const uint32_t ch = smem_u32(st), cl = smem_u32(st + S::C_BYTES);
-        const uint32_t ho = (uint32_t)h * S::HALF_BYTES;
+        const uint64_t dch = dC0 + (uint64_t)((s * S::C_STAGE) >> 4);
+        const uint64_t dph = dPhi + (uint64_t)((h * S::HALF_BYTES) >> 4);
         const uint32_t d = tmem + (uint32_t)(sb * 128);
 #pragma unroll
         for (int ks = 0; ks < KP / 16; ++ks) {
-          const uint32_t ko = (uint32_t)ks * 256u;
-          const uint64_t dch = smem_desc(ch + ko, 128, S::SBO_K);
-          const uint64_t dcl = smem_desc(cl + ko, 128, S::SBO_K);
-          const uint64_t dph = smem_desc(phh + ho + ko, 128, S::SBO_K);
-          const uint64_t dpl = smem_desc(phl + ho + ko, 128, S::SBO_K);
-          mma_f16(d, dch, dph, IDESC1, ks > 0 ? 1u : 0u);
-          mma_f16(d, dch, dpl, IDESC1, 1u);
-          mma_f16(d, dcl, dph, IDESC1, 1u);
+          const uint64_t ko = (uint64_t)ks * 16u;  // 256 bytes per K step
+          mma_f16(d, dch + ko, dph + ko, IDESC1, ks > 0 ? 1u : 0u);
+          mma_f16(d, dch + ko, dph + PHI_LO + ko, IDESC1, 1u);
+          mma_f16(d, dch + C_LO + ko, dph + ko, IDESC1, 1u);
         }
         mma_commit(&s_full[sb]);
         if (h == nh - 1) mma_commit(&coef_empty[s]);
@@ -360,16 +391,15 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
           return false;
         fence_after_sync();
         const uint32_t d = tmem + S::TM_D2 + (uint32_t)(db * NPSI);
+        const uint32_t e0 = tmem + (uint32_t)(sb * 128);
+        const uint64_t dsh = dPsi + (uint64_t)(16 * h) * 8u;
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {  // 16 queries per K step
-          const uint32_t eh = tmem + (uint32_t)(sb * 128 + 32 * (kk >> 1) + 8 * (kk & 1));
-          const uint32_t el = eh + 16u;
-          const uint32_t qo = (uint32_t)(16 * h + 2 * kk) * 128u;
-          const uint64_t dsh = smem_desc(psh + qo, 128, S::SBO_Q);
-          const uint64_t dsl = smem_desc(psl + qo, 128, S::SBO_Q);
-          mma_f16_ts(d, eh, dsh, IDESC2, (h > 0 || kk > 0) ? 1u : 0u);
-          mma_f16_ts(d, eh, dsl, IDESC2, 1u);
-          mma_f16_ts(d, el, dsh, IDESC2, 1u);
+          const uint32_t eh = e0 + (uint32_t)(32 * (kk >> 1) + 8 * (kk & 1));
+          const uint64_t qo = (uint64_t)(2 * kk) * 8u;
+          mma_f16_ts(d, eh, dsh + qo, IDESC2, (h > 0 || kk > 0) ? 1u : 0u);
+          mma_f16_ts(d, eh, dsh + PSI_LO + qo, IDESC2, 1u);
+          mma_f16_ts(d, eh + 16u, dsh + qo, IDESC2, 1u);
         }
         if (h == nh - 1) mma_commit(&d2_full[db]);
         return true;
@@ -382,27 +412,32 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
       if (!ok) fail();
     }
   } else {
-    // ---- epilogue and chain
+    // ---- epilogue: E = 2^S written back in place as FP16 hi / lo
     const int quad = warp & 3, grp = (warp - 4) >> 2;
     const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
     const int j = quad * 32 + lane;  // candidate lane
+    float hsc[N];
+#pragma unroll
+    for (int d = 0; d < N; ++d) hsc[d] = sh[d];
+    // Chain of entry (candidate j, chunk ic): from D2 = sum_q e dy' phi' the
+    // lifted-coefficient gradient Gc, then the frame-free record
+    // [G = dl/dA (symmetric, lower packed), v = Gc0 m~ - G_lin, dl/dw];
+    // dl/dM = 2 M sum G and dl/dm = 2 A sum v follow per Gaussian.
     auto chain = [&](int ic) -> bool {
-      const int db = ic & 1;
+      const int db = ic & 1, s = ic % CS;
+      const float4* stp = reinterpret_cast<const float4*>(Cst + s * S::C_STAGE + 2 * S::C_BYTES +
+                                                          NC * 4 + (uint32_t)j * S::STASH);
+      float sv[12];
+      {
+        const float4 v0 = stp[0], v1 = stp[1], v2 = stp[2];
+        sv[0] = v0.x; sv[1] = v0.y; sv[2] = v0.z; sv[3] = v0.w;
+        sv[4] = v1.x; sv[5] = v1.y; sv[6] = v1.z; sv[7] = v1.w;
+        sv[8] = v2.x; sv[9] = v2.y; sv[10] = v2.z; sv[11] = v2.w;
+      }
+      warp_arrive(&coef_empty[s]);
+      const int slot = __float_as_int(sv[N + 3]);
       if (!warp_wait(&d2_full[db], (ic >> 1) & 1, abort_flag)) return false;
       fence_after_sync();
-      const long long c0 = beg + (long long)ic * NC;
-      const long long e = c0 + j;
-      const int g = e < end ? a.ids[e] : -1;
-      const bool live = (unsigned)g < (unsigned)a.Ge;
-      float hd[S::R];
-      {
-        const float4* src = reinterpret_cast<const float4*>(a.rec + (size_t)(live ? g : 0) * R2);
-#pragma unroll
-        for (int k = 0; k < R4; ++k) {
-          const float4 v = live ? __ldg(src + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-          hd[4 * k] = v.x; hd[4 * k + 1] = v.y; hd[4 * k + 2] = v.z; hd[4 * k + 3] = v.w;
-        }
-      }
       // Gc_k = sum_c w_c D2[c][k], dl/dw_c = D2[c][P + N]
       float Gc[F], gw[3];
 #pragma unroll
@@ -416,20 +451,17 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
         tmem_wait_ld();
 #pragma unroll
         for (int cb = 0; cb < KP; cb += 16) tmem_reg_fence16(v + cb);
-        const float wc = hd[P + N + c];
+        const float wc = sv[N + c];
 #pragma unroll
         for (int k = 0; k < F; ++k) Gc[k] = fmaf(wc, __uint_as_float(v[k]), Gc[k]);
         gw[c] = __uint_as_float(v[P + N]);
       }
       fence_before_sync();
       warp_arrive(&d2_empty[db]);
-      if (!live) return true;
+      if (slot < 0) return true;
       // back to the unscaled features and dy (Psi held dy / dys):
       // Gc = -1/2 h_k dys sum_c w_c D2
       const float gsc = -0.5f * s_dys;
-      float hsc[N];
-#pragma unroll
-      for (int d = 0; d < N; ++d) hsc[d] = sh[d];
 #pragma unroll
       for (int d = 0; d < N; ++d)
 #pragma unroll
@@ -437,62 +469,29 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
 #pragma unroll
       for (int d = 0; d < N; ++d) Gc[P + d] *= gsc * hsc[d];
       Gc[P + N] *= gsc;
-      float mt[N];
-#pragma unroll
-      for (int d = 0; d < N; ++d) mt[d] = hd[P + d] - sctr[d];
       const float Gc0 = Gc[P + N];
       float rec[RP];
-      // dl/dm = dl/dm~ = 2 A (Gc0 m~ - G_lin)
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        float s2 = 0.0f;
-#pragma unroll
-        for (int k = 0; k < N; ++k)
-          s2 = fmaf(hd[i >= k ? tri(i) + k : tri(k) + i], Gc0 * mt[k] - Gc[P + k], s2);
-        rec[P + i] = 2.0f * s2;
-      }
-      // symmetric gradient with respect to A (all matrix entries)
-      float Gf[N][N];
 #pragma unroll
       for (int i = 0; i < N; ++i)
 #pragma unroll
         for (int k = 0; k <= i; ++k) {
-          float gv;
-          if (i == k)
-            gv = Gc[tri(i) + i] - 2.0f * Gc[P + i] * mt[i] + Gc0 * mt[i] * mt[i];
-          else
-            gv = Gc[tri(i) + k] - (Gc[P + i] * mt[k] + Gc[P + k] * mt[i]) + Gc0 * mt[i] * mt[k];
-          Gf[i][k] = gv;
-          Gf[k][i] = gv;
+          const float mi = sv[i], mk = sv[k];
+          rec[tri(i) + k] =
+              (i == k) ? Gc[tri(i) + i] - 2.0f * Gc[P + i] * mi + Gc0 * mi * mi
+                       : Gc[tri(i) + k] - (Gc[P + i] * mk + Gc[P + k] * mi) + Gc0 * mi * mk;
         }
-      // dl/dM = 2 M G (lower part), M from the record tail
-      float M[P];
-      {
-        const float* src = a.rec + (size_t)g * R2 + S::R;
 #pragma unroll
-        for (int k = 0; k < P; ++k) M[k] = __ldg(src + k);
-      }
-#pragma unroll
-      for (int i = 0; i < N; ++i)
-#pragma unroll
-        for (int k = 0; k <= i; ++k) {
-          float s2 = 0.0f;
-#pragma unroll
-          for (int l = 0; l <= i; ++l) s2 = fmaf(M[tri(i) + l], Gf[l][k], s2);
-          rec[tri(i) + k] = 2.0f * s2;
-        }
+      for (int i = 0; i < N; ++i) rec[P + i] = Gc0 * sv[i] - Gc[P + i];
 #pragma unroll
       for (int c = 0; c < 3; ++c) rec[P + N + c] = gw[c] * s_dys;
 #pragma unroll
       for (int k = P + N + 3; k < RP; ++k) rec[k] = 0.0f;
-      const long long slot = a.slot ? (long long)a.slot[e] : e;
       float* out = a.part + (size_t)slot * RP;
 #pragma unroll
       for (int k = 0; k < RP; k += 4)
         *reinterpret_cast<float4*>(out + k) = make_float4(rec[k], rec[k + 1], rec[k + 2], rec[k + 3]);
       return true;
     };
-
     float back = 1.0f;
     bool ok = true;
     for (int u = 0; u < U; ++u) {
@@ -505,28 +504,31 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
         back = reinterpret_cast<const float*>(Cst + s * S::C_STAGE + 2 * S::C_BYTES)[j];
         warp_arrive(&coef_empty[s]);
       }
-#pragma unroll 1
+      // all 64 columns of this warp in flight at once, one wait
+      const uint32_t col = tmem + lane_off + (uint32_t)(sb * 128 + grp * 64);
+      uint32_t v[64];
+#pragma unroll
+      for (int cb = 0; cb < 64; cb += 16) tmem_ld16_nowait(col + (uint32_t)cb, v + cb);
+      tmem_wait_ld();
+#pragma unroll
+      for (int cb = 0; cb < 64; cb += 16) tmem_reg_fence16(v + cb);
+#pragma unroll
       for (int cb = 0; cb < 64; cb += 32) {
-        const uint32_t col = tmem + lane_off + (uint32_t)(sb * 128 + grp * 64 + cb);
-        uint32_t v[32];
-        tmem_ld16_nowait(col, v);
-        tmem_ld16_nowait(col + 16u, v + 16);
-        tmem_wait_ld();
-        tmem_reg_fence16(v);
-        tmem_reg_fence16(v + 16);
         uint32_t hi[16], lo[16];
 #pragma unroll
         for (int p = 0; p < 16; ++p) {
-          const float2 sv = __fmul2_rn(make_float2(__uint_as_float(v[2 * p]), __uint_as_float(v[2 * p + 1])),
+          const float2 sv = __fmul2_rn(make_float2(__uint_as_float(v[cb + 2 * p]),
+                                                   __uint_as_float(v[cb + 2 * p + 1])),
                                        make_float2(back, back));
           split_h2b(ex2_approx(sv.x), ex2_approx(sv.y), hi[p], lo[p]);
         }
-        tmem_st16(col, hi);
-        tmem_st16(col + 16u, lo);
+        tmem_st16(col + (uint32_t)cb, hi);
+        tmem_st16(col + (uint32_t)cb + 16u, lo);
       }
       tmem_wait_st();
       fence_before_sync();
       warp_arrive(&e_full[sb]);
+      // chain of the previous chunk, by the group of its parity
       if (h == nh - 1 && i >= 1 && ((i - 1) & 1) == grp) {
         ok = chain(i - 1);
         if (!ok) break;

@@ -458,6 +458,39 @@ __device__ __forceinline__ void raw_weight_grad(const float* Gw, float araw, con
   *ga = s;
 }
 
+// Record kind 1 to kind 0: dl/dM = 2 M G (lower part; G symmetric, lower
+// packed) and dl/dm = 2 A v with A = M^T M.
+template <int N>
+__device__ __forceinline__ void part_to_dM(const float* M, const float* sp, float* out) {
+  constexpr int P = tri(N);
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int k = 0; k <= i; ++k) {
+      float s = 0.0f;
+#pragma unroll
+      for (int l = 0; l <= i; ++l) s = fmaf(M[tri(i) + l], sp[l >= k ? tri(l) + k : tri(k) + l], s);
+      out[tri(i) + k] = 2.0f * s;
+    }
+  float Mv[N];  // M v, then A v = M^T (M v)
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float s = 0.0f;
+#pragma unroll
+    for (int l = 0; l <= i; ++l) s = fmaf(M[tri(i) + l], sp[P + l], s);
+    Mv[i] = s;
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    float s = 0.0f;
+#pragma unroll
+    for (int i = k; i < N; ++i) s = fmaf(M[tri(i) + k], Mv[i], s);
+    out[P + k] = 2.0f * s;
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) out[P + N + c] = sp[P + N + c];
+}
+
 template <int N>
 __global__ void __launch_bounds__(128) chain_kernel(ChainArgs a) {
   constexpr int P = tri(N), RP = part_floats(N);
@@ -467,12 +500,17 @@ __global__ void __launch_bounds__(128) chain_kernel(ChainArgs a) {
   act_lower32<N>(a.theta + (size_t)g * P, L);
   inv_lower<N>(L, M);
   const float* sp = a.gsum + (size_t)g * RP;
+  float conv[P + N + 3];
+  if (a.part_kind == 1) {
+    part_to_dM<N>(M, sp, conv);
+    sp = conv;
+  }
   grad_L<N>(M, sp, GL);
 #pragma unroll
   for (int i = 0; i < N; ++i) Gm[i] = sp[P + i];
   if (a.has_children) {
     const float* sc = a.gsum + (size_t)(a.G + g) * RP;
-    float U[P], Lc[P], Mc[P], GLc[P], Gmc[N], mu[N];
+    float U[P], Lc[P], Mc[P], GLc[P], Gmc[N], mu[N], convc[P + N + 3];
     act_lower32<N>(a.u_theta + (size_t)g * P, U);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -486,6 +524,10 @@ __global__ void __launch_bounds__(128) chain_kernel(ChainArgs a) {
       }
     }
     inv_lower<N>(Lc, Mc);
+    if (a.part_kind == 1) {
+      part_to_dM<N>(Mc, sc, convc);
+      sc = convc;
+    }
     grad_L<N>(Mc, sc, GLc);
 #pragma unroll
     for (int i = 0; i < N; ++i) Gmc[i] = sc[P + i];

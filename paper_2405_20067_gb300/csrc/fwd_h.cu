@@ -236,7 +236,10 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
     float4 cur[R4], nxt[R4];
     load(cand(0), cur);
     int g_next = cand(1);
-    const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo);
+    // descriptor bases (a descriptor for base + off is base + off / 16)
+    const uint64_t dA0 = smem_desc(smem_u32(Ahi), 128, S::SBO);
+    const uint64_t dB0 = smem_desc(smem_u32(Cst), 128, S::SBO);
+    constexpr uint64_t A_LO = S::PHI_BYTES >> 4, B_LO = S::B_BYTES >> 4;
     constexpr uint32_t IDESC = idesc_f16(NC);
     for (int i = 0; i < nchunks; ++i) {
       const int s = i % CS;
@@ -313,20 +316,16 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
           fail();
         } else {
           fence_after_sync();
-          const uint32_t bh = smem_u32(st), bl = smem_u32(st + S::B_BYTES);
+          const uint64_t dbh = dB0 + (uint64_t)((s * S::C_STAGE) >> 4);
           for (int h = 0; h < nh; ++h) {
             const uint32_t d = tmem + (uint32_t)(b * 256 + h * 128);
-            const uint32_t ho = (uint32_t)h * S::HALF_BYTES;
+            const uint64_t dah = dA0 + (uint64_t)((h * S::HALF_BYTES) >> 4);
 #pragma unroll
             for (int ks = 0; ks < KP / 16; ++ks) {
-              const uint32_t ko = (uint32_t)ks * 256u;  // two 16-byte core matrices per K step
-              const uint64_t dah = smem_desc(ah + ho + ko, 128, S::SBO);
-              const uint64_t dal = smem_desc(al + ho + ko, 128, S::SBO);
-              const uint64_t dbh = smem_desc(bh + ko, 128, S::SBO);
-              const uint64_t dbl = smem_desc(bl + ko, 128, S::SBO);
-              mma_f16(d, dah, dbh, IDESC, ks > 0 ? 1u : 0u);
-              mma_f16(d, dah, dbl, IDESC, 1u);
-              mma_f16(d, dal, dbh, IDESC, 1u);
+              const uint64_t ko = (uint64_t)ks * 16u;  // two 16-byte core matrices per K step
+              mma_f16(d, dah + ko, dbh + ko, IDESC, ks > 0 ? 1u : 0u);
+              mma_f16(d, dah + ko, dbh + B_LO + ko, IDESC, 1u);
+              mma_f16(d, dah + A_LO + ko, dbh + ko, IDESC, 1u);
             }
           }
           mma_commit(&acc_full[b]);

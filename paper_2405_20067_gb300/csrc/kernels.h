@@ -64,6 +64,8 @@ struct BwdArgs {
 struct ChainArgs {
   int G, has_children;
   const float* gsum;         // [Ge][part_floats(N)]
+  int part_kind;             // 0: [dl/dM, dl/dm, dl/dw]; 1: [G = dl/dA, v, dl/dw] with
+                             //    dl/dM = 2 M G, dl/dm = 2 A v (A = M^T M)
   const float *theta, *alpha_raw, *color_raw, *u_theta, *m_u, *c_alpha_raw, *c_color_raw;
   float *g_mean, *g_theta, *g_alpha, *g_color, *g_u_theta, *g_m_u, *g_c_alpha, *g_c_color;
 };
