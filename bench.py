@@ -47,6 +47,13 @@ def workload_name(g, q):
             f"cutoff 1/255, {BUCKETS} buckets, Adam lr 1e-3")
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one bwd_h_kernel<6> launch,
+# scaled from the ncu capture of the same kernel on the 1/8 workload to a
+# full launch by the candidate entries processed (profiles/bwd_h_kernel_fit_n6.md);
+# None until a capture of the current kernel exists.
+BWD_TRAFFIC = None
+
+
 def flops_per_pair(N: int):
     """Algorithmic FP32 flops per Gaussian-query pair (FMA = 2):
     forward  d = x - m (N), z = M d (N(N+1)), s = |z|^2 (2N), scale (1),
@@ -55,6 +62,19 @@ def flops_per_pair(N: int):
              beta z (N), sum beta z (N), sum beta z d^T (N(N+1))
                                                      -> 2N^2 + 7N + 13."""
     return N * N + 4 * N + 7, 2 * N * N + 7 * N + 13
+
+
+def tc_flops_per_pair(N: int):
+    """Tensor-core flops per pair.  Algorithmic (the lifted contraction
+    counted once): forward 2F (s = phi . coef), backward 4F (s recomputed and
+    the gradient contraction sum_q beta phi), F = N(N+1)/2 + N + 1.
+    Executed by the kernels (FP16 hi/lo split, three products, K padded to
+    KP = 16 ceil(F / 16)): forward 6 KP; backward 6 KP for S plus 18 KP for
+    D2 = E Psi (Psi has 3 KP columns, one block per colour)."""
+    P = N * (N + 1) // 2
+    F = P + N + 1
+    KP = (F + 15) // 16 * 16
+    return 2 * F, 4 * F, 6 * KP, 6 * KP + 18 * KP
 
 
 def fp32_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
@@ -384,20 +404,43 @@ def main():
     if not args.no_fp32_form:
         plain = run_fit("fp32", max(3, args.steps // 2), 3, device, flush, world, 0)
     fwd_f, bwd_f = flops_per_pair(N_DIM)
+    alg_fwd, alg_bwd, exe_fwd, exe_bwd = tc_flops_per_pair(N_DIM)
     mean_pairs = chosen["pairs_per_step"]
     kern = chosen["kernels_ms"]
     peak_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = fp32_peak_tflops(peak_mhz)
-    achieved = mean_pairs * bwd_f / (kern["backward"] / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": ("bwd_tc_kernel<6>" if args.bwd_form == "tc" else
-                                           "bwd_kernel<6> (per-pair partials, FP32 pipe)"),
-                "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz "
-                               f"(clock from {peak_kind} peaks file)"}
+    fp32_peak = fp32_peak_tflops(peak_mhz)
+    tc_peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0)))
+    t_bwd = kern["backward"] / 1e3
+    t_fwd = kern["forward"] / 1e3
     kernels = {n: {"ms": round(v, 4)} for n, v in kern.items()}
-    kernels["backward"]["fp32_tflops"] = round(achieved, 3)
-    kernels["forward"]["form"] = "lifted tensor-core (tcgen05 TF32x3)"
+    if args.bwd_form == "tc":
+        achieved = mean_pairs * alg_bwd / t_bwd / 1e12
+        executed = mean_pairs * exe_bwd / t_bwd / 1e12
+        roofline = {"bound": "tensor", "kernel": f"bwd_h_kernel<{N_DIM}> (tcgen05 kind::f16)",
+                    "achieved": round(achieved, 3), "peak": round(tc_peak, 1), "unit": "TFLOP/s",
+                    "frac": round(achieved / tc_peak, 4), "traffic": BWD_TRAFFIC,
+                    "peak_source": f"bf16 dense sustained, {peak_kind} (FP16 operands run at "
+                                   "the bf16 rate)",
+                    "algorithmic": f"{alg_bwd} flop/pair (4F: recompute s, gradient contraction)",
+                    "executed_tflops": round(executed, 2),
+                    "executed_frac": round(executed / tc_peak, 4),
+                    "executed_note": f"{exe_bwd} MMA flop/pair issued: FP16 hi/lo split (3 "
+                                     "products) and the colour-blocked Psi operand",
+                    "mufu_ex2_per_s": mean_pairs / t_bwd}
+    else:
+        achieved = mean_pairs * bwd_f / t_bwd / 1e12
+        roofline = {"bound": "alu", "kernel": f"bwd_kernel<{N_DIM}> (per-pair partials, FP32 pipe)",
+                    "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                    "frac": round(achieved / fp32_peak, 4), "traffic": None,
+                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz "
+                                   f"(clock from {peak_kind} peaks file)"}
+    kernels["backward"]["form"] = ("tensor-core (tcgen05 FP16x3, E Psi contraction)"
+                                   if args.bwd_form == "tc" else "FP32 per-pair partials")
+    kernels["backward"]["fp32_equiv_tflops"] = round(mean_pairs * bwd_f / t_bwd / 1e12, 3)
+    kernels["forward"]["form"] = "lifted tensor-core (tcgen05 FP16x3)"
+    kernels["forward"]["tc_alg_tflops"] = round(mean_pairs * alg_fwd / t_fwd / 1e12, 3)
+    kernels["forward"]["tc_executed_tflops"] = round(mean_pairs * exe_fwd / t_fwd / 1e12, 2)
+    kernels["forward"]["fp32_equiv_tflops"] = round(mean_pairs * fwd_f / t_fwd / 1e12, 3)
     if rank != 0:
         return
     out = {"metric": METRIC, "value": chosen["value"], "unit": UNIT, "n_gpus": world,

@@ -393,9 +393,9 @@ ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q, const ndg_
   pa.rec_kind = mode == NDG_MODE_TC ? 2 : 0;
   pa.status = &reinterpret_cast<WsHeader*>(w + c.header)->status;
   tr += launch_prep(N, pa, s);
-  // Transpose the candidate lists to Gaussian-major order first (stable
-  // radix sort of the entries by Gaussian index), so that the per-entry
-  // partial records can be written straight to their Gaussian-major slots.
+  // Gaussian-major order of the entries (stable radix sort by Gaussian
+  // index): the per-entry partial records are written in entry order and
+  // summed per Gaussian through this permutation.
   const int Ge = pa.Ge;
   uint32_t* sk;
   int32_t* sv;
@@ -404,10 +404,6 @@ ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q, const ndg_
                          cull->E_cap, cull->E_dev, bits_for(Ge > 0 ? Ge : 1), w + L.tmp, s, &sk, &sv);
   long long* goff = (long long*)(w + L.goff);
   tr += bin_boundaries(sk, cull->E_cap, cull->E_dev, Ge, goff, s);
-  // the key buffer that does not hold the sorted keys is free: reuse it for
-  // the inverse permutation
-  int32_t* slot = (int32_t*)(sk == (uint32_t*)(w + L.sk_a) ? w + L.sk_b : w + L.sk_a);
-  tr += launch_invert_perm(sv, cull->E_cap, cull->E_dev, slot, s);
   BwdArgs ba{};
   ba.x = q->x;
   ba.dy = dy;
@@ -417,14 +413,14 @@ ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q, const ndg_
   ba.ids = cull->ids;
   ba.rec = pa.rec;
   ba.Ge = pa.Ge;
-  ba.slot = slot;
+  ba.slot = nullptr;
   ba.part = (float*)(w + L.part);
   ba.status = pa.status;
   tr.begin();
   tr += mode == NDG_MODE_TC ? launch_bwd_h(N, ba, z.T, s) : launch_bwd(N, ba, z.T, s);
   tr.end();
   float* gsum = (float*)(w + L.gsum);
-  tr += launch_segsum(ba.part, part_floats(N), goff, Ge, gsum, s);
+  tr += launch_segsum(ba.part, part_floats(N), goff, Ge, sv, gsum, s);
   ChainArgs ch{};
   ch.G = mix->G;
   ch.has_children = mix->has_children;

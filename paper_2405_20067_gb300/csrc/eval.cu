@@ -339,12 +339,15 @@ __global__ void __launch_bounds__(128) bwd_kernel(BwdArgs a) {
 }
 
 // ---- per-Gaussian sums of the partial records (Gaussian-major, fixed order) --
-// One warp per evaluated Gaussian; its records are contiguous (slots
-// goff[e] .. goff[e+1]).  Lanes are split into groups of RP/4 (one float4
-// column each) that take every G-th record; the groups' sums are combined
-// in group order, so the result does not depend on scheduling.
+// One warp per evaluated Gaussian; its records are positions goff[e] ..
+// goff[e+1] of the Gaussian-major order, i.e. records perm[j] (entry order)
+// for j in that range (the stable sort keeps entries in tile order).  Lanes
+// are split into groups of RP/4 (one float4 column each) that take every
+// G-th record; the groups' sums are combined in group order, so the result
+// does not depend on scheduling.
 __global__ void __launch_bounds__(256) segsum_kernel(const float* __restrict__ part, int RP,
                                                      const long long* __restrict__ goff, int Ge,
+                                                     const int32_t* __restrict__ perm,
                                                      float* __restrict__ gsum) {
   __shared__ float4 sh[8][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -357,7 +360,8 @@ __global__ void __launch_bounds__(256) segsum_kernel(const float* __restrict__ p
     const long long b = goff[e], en = goff[e + 1];
     const float4* src = reinterpret_cast<const float4*>(part);
     for (long long j = b + grp; j < en; j += G) {
-      const float4 v = __ldg(src + j * RP4 + col);
+      const long long r = perm ? (long long)__ldg(perm + j) : j;
+      const float4 v = __ldg(src + r * RP4 + col);
       acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
     }
   }
@@ -371,15 +375,6 @@ __global__ void __launch_bounds__(256) segsum_kernel(const float* __restrict__ p
     }
     reinterpret_cast<float4*>(gsum)[e * RP4 + lane] = s;
   }
-}
-
-// Entry -> Gaussian-major slot: slot[gidx[p]] = p.
-__global__ void invert_perm_kernel(const int32_t* __restrict__ gidx, long long n_cap,
-                                   const long long* __restrict__ n_dev, int32_t* __restrict__ slot) {
-  long long n = *n_dev < n_cap ? *n_dev : n_cap;
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-       p += (long long)gridDim.x * blockDim.x)
-    slot[gidx[p]] = (int32_t)p;
 }
 
 // ---- chain rule to the raw parameters --------------------------------------------
@@ -623,18 +618,10 @@ int launch_bwd(int N, const BwdArgs& a, long long T, cudaStream_t s) {
   return 1;
 }
 
-int launch_segsum(const float* part, int RP, const long long* goff, int Ge, float* gsum,
-                  cudaStream_t s) {
+int launch_segsum(const float* part, int RP, const long long* goff, int Ge, const int32_t* perm,
+                  float* gsum, cudaStream_t s) {
   if (Ge <= 0) return 0;
-  segsum_kernel<<<(unsigned)ceil_div<long long>(Ge, 8), 256, 0, s>>>(part, RP, goff, Ge, gsum);
-  return 1;
-}
-
-int launch_invert_perm(const int32_t* gidx, long long n_cap, const long long* n_dev, int32_t* slot,
-                       cudaStream_t s) {
-  long long blocks = ceil_div<long long>(n_cap > 0 ? n_cap : 1, 256);
-  if (blocks > 65535) blocks = 65535;
-  invert_perm_kernel<<<(unsigned)blocks, 256, 0, s>>>(gidx, n_cap, n_dev, slot);
+  segsum_kernel<<<(unsigned)ceil_div<long long>(Ge, 8), 256, 0, s>>>(part, RP, goff, Ge, perm, gsum);
   return 1;
 }
 

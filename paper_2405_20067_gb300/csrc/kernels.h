@@ -57,7 +57,7 @@ struct BwdArgs {
   const float* rec;
   int Ge;
   int* status;               // device status word (timeouts of bounded waits)
-  const int32_t* slot;       // entry -> Gaussian-major slot, or null (entry order)
+  const int32_t* slot;       // entry -> output record index, or null (entry order)
   float* part;               // [E_cap][part_floats(N)]
 };
 
@@ -120,10 +120,8 @@ size_t fwd_tc_smem(int N);
 int launch_loss(const float* y, const float* target, float* dy, long long n, double* part,
                  double* loss, cudaStream_t s);
 int launch_bwd(int N, const BwdArgs& a, long long T, cudaStream_t s);
-int launch_segsum(const float* part, int RP, const long long* goff, int Ge, float* gsum,
-                 cudaStream_t s);
-int launch_invert_perm(const int32_t* gidx, long long n_cap, const long long* n_dev, int32_t* slot,
-                       cudaStream_t s);
+int launch_segsum(const float* part, int RP, const long long* goff, int Ge, const int32_t* perm,
+                 float* gsum, cudaStream_t s);
 int launch_chain(int N, const ChainArgs& a, cudaStream_t s);
 int launch_adam(const AdamArgs& a, cudaStream_t s);
 int launch_densify(int N, const DensifyArgs& a, cudaStream_t s);
