@@ -47,11 +47,11 @@ def workload_name(g, q):
             f"cutoff 1/255, {BUCKETS} buckets, Adam lr 1e-3")
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one bwd_h_kernel<6> launch,
-# scaled from the ncu capture of the same kernel on the 1/8 workload to a
-# full launch by the candidate entries processed (profiles/bwd_h_kernel_fit_n6.md);
-# None until a capture of the current kernel exists.
-BWD_TRAFFIC = None
+# dram__bytes_read.sum + dram__bytes_write.sum of one bwd_h_kernel<6> launch
+# (18.75 MB + 303.83 MB on the 1/8 workload, E = 2,760,083 entries), scaled to
+# a full launch by the entries processed (E = 1.0894e8, x 39.47); taken from
+# profiles/bwd_h_kernel_fit_n6.md and to be re-taken whenever the kernel changes.
+BWD_TRAFFIC = 12.73e9
 
 
 def flops_per_pair(N: int):
