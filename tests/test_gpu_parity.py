@@ -87,6 +87,8 @@ TC_CASES = [
     (3, 500, 5000, 64, 2, 0.0, 32, False),
     (1, 200, 2000, 256, 1, 1 / 255, 64, False),
     (12, 400, 2000, 256, 24, 1 / 255, 16, False),
+    (8, 800, 6000, 256, 16, 1 / 255, 64, True),
+    (5, 500, 4000, 200, 8, 0.0, 32, False),
 ]
 
 
@@ -104,6 +106,7 @@ def test_tc_forward_matches_oracle(ndg, oracle, N, G, Q, tile, k, cutoff, B, chi
     assert E == offs[-1]
     yo = oracle.eval(L, m, w, x.astype(np.float64), tile, offs, ids)
     worst = assert_outputs_close(y, yo, rtol=1e-3, floor=1e-3, what="tensor-core forward")
+    print(f"tc forward N={N} tile={tile}: worst relative error {worst:.2e}")
     print(f"N={N} tile={tile}: worst relative error {worst:.2e}")
     assert ndg.read_status(ev.ws) == 0
 
