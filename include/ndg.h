@@ -142,9 +142,11 @@ ndg_status ndg_build_cull(const ndg_mixture* mix, const ndg_queries* q,
 
 #define NDG_MODE_FP32 0 /* centred form z = L^{-1}(x - m) on the FP32 pipe */
 #define NDG_MODE_TC 1   /* lifted quadratic form on the tensor cores: s =
-                           phi(x - c) . coef with phi = [x x^T (lower), x, 1],
-                           coef from A = V^-1, split TF32 (3 products), FP32
-                           accumulation; about 1e-5 relative on s's scale */
+                           phi(x - c) . coef with phi = [x x^T (lower), x, 1]
+                           about the tile centre c, coef from A = V^-1; FP16
+                           hi/lo operands (3 products) with exact power-of-two
+                           scaling, FP32 accumulation; N <= 12; outputs within
+                           ~2e-4 relative of the FP64 definition */
 
 /* Eq. 1 and Eq. 8: y [Q][3] = culled mixture sum at every query.  `cull`
  * must come from ndg_build_cull on the same mixture and queries. */
@@ -166,8 +168,9 @@ ndg_status ndg_loss_l2(long long Q, const float* y, const float* target,
  * the raw parameters and `cull`; per-Gaussian sums run in a fixed order
  * (no atomics), so results are bit-reproducible.  Requires E < 2^31.
  * mode NDG_MODE_FP32: centred form on the FP32 pipe; NDG_MODE_TC: the
- * lifted form on the tensor cores (gradient of the lifted coefficients as
- * a second GEMM), available for N <= 6 (shared-memory bound). */
+ * lifted form on the tensor cores (the gradients of the lifted coefficients
+ * and of w as a second contraction E Psi with Psi = dy (x) phi), available
+ * for N <= 6 (shared-memory bound); other N return NDG_ERR_INVALID_ARG. */
 ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q,
                         const ndg_cull* cull, int mode, const float* dy,
                         ndg_mixture* grad, void* ws, size_t ws_bytes,

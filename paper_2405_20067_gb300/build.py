@@ -18,8 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libndg.so")
-SOURCES = ["primitives.cu", "cull.cu", "eval.cu", "train.cu", "api.cu", "noalloc.cu", "tc.cu",
-           "fwd_h.cu", "bwd_h.cu"]
+SOURCES = ["primitives.cu", "cull.cu", "eval.cu", "train.cu", "api.cu", "noalloc.cu", "fwd_h.cu",
+           "bwd_h.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

@@ -1,5 +1,5 @@
 // fwd_h.cu -- lifted-feature evaluation on the tensor cores with FP16
-// operands split into high and low halves (ndg_forward, NDG_MODE_TC, N <= 8).
+// operands split into high and low halves (ndg_forward, NDG_MODE_TC).
 //
 // Same quadratic-form evaluation as the TF32 kernels: for a tile with centre
 // c the exponent of Eq. 1 is  s = phi(x~) . coef  with lifted features
@@ -55,7 +55,7 @@ struct FwdHShape {
   static constexpr int KP = (F + 15) / 16 * 16;  // K step of kind::f16 is 16
   static constexpr int NC = 128;                 // candidates per chunk (MMA N)
   static constexpr int R = rec_floats(N);
-  static constexpr int CS = N <= 6 ? 4 : 3;      // coefficient stages
+  static constexpr int CS = N <= 6 ? 4 : (N <= 8 ? 3 : 2);  // coefficient stages
   static constexpr uint32_t SBO = (KP / 8) * 128;  // 8-row group stride (bytes)
   static constexpr uint32_t PHI_BYTES = 256u * KP * 2;  // one of hi / lo, 256 rows
   static constexpr uint32_t HALF_BYTES = 128u * KP * 2; // one 128-row block
@@ -233,7 +233,11 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
         for (int k = 0; k < R4; ++k) r[k] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     };
-    float4 cur[R4], nxt[R4];
+    // N <= 8: the records of chunk i + 1 are loaded into registers while
+    // chunk i is built; larger records are loaded right after a build (the
+    // latency overlaps the next stage wait) to keep the register count down.
+    constexpr bool PRE = N <= 8;
+    float4 cur[R4], nxt[PRE ? R4 : 1];
     load(cand(0), cur);
     int g_next = cand(1);
     // descriptor bases (a descriptor for base + off is base + off / 16)
@@ -243,8 +247,10 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
     constexpr uint32_t IDESC = idesc_f16(NC);
     for (int i = 0; i < nchunks; ++i) {
       const int s = i % CS;
-      load(g_next, nxt);  // chunk i + 1 (zeros past the end)
-      g_next = cand(i + 2);
+      if constexpr (PRE) {
+        load(g_next, nxt);  // chunk i + 1 (zeros past the end)
+        g_next = cand(i + 2);
+      }
       bool ok = true;
       if (i >= CS) ok = warp_wait(&coef_empty[s], ((i / CS) - 1) & 1, abort_flag);
       if (!ok && lane == 0) fail();
@@ -257,7 +263,7 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
           buf[4 * k] = cur[k].x; buf[4 * k + 1] = cur[k].y;
           buf[4 * k + 2] = cur[k].z; buf[4 * k + 3] = cur[k].w;
         }
-        float coef[KP], mt[N];
+        float mt[N], tA[N];
 #pragma unroll
         for (int d = 0; d < N; ++d) mt[d] = buf[P + d] - sctr[d];
         float cst = 0.0f;
@@ -266,32 +272,44 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
           float s2 = 0.0f;
 #pragma unroll
           for (int k = 0; k < N; ++k) s2 = fmaf(buf[d >= k ? tri(d) + k : tri(k) + d], mt[k], s2);
-          coef[P + d] = (kNegHalfLog2eH * -2.0f) * s2 * hsc[d];
+          tA[d] = s2;
           cst = fmaf(mt[d], s2, cst);
         }
-#pragma unroll
-        for (int d = 0; d < N; ++d)
-#pragma unroll
-          for (int k = 0; k <= d; ++k)
-            coef[tri(d) + k] = kNegHalfLog2eH * (d == k ? buf[tri(d) + k] : 2.0f * buf[tri(d) + k]) *
-                               (hsc[d] * hsc[k]);
-        coef[P + N] = kNegHalfLog2eH * cst;
-#pragma unroll
-        for (int k = P + N + 1; k < KP; ++k) coef[k] = 0.0f;
+        // coefficient k (compile-time after unrolling): quadratic (d, e),
+        // linear d, constant, zero padding
+        auto cf = [&](int k) -> float {
+          if (k < P) {
+            int d = 0;
+            while (tri(d + 1) <= k) ++d;
+            const int e2 = k - tri(d);
+            return kNegHalfLog2eH * (d == e2 ? buf[k] : 2.0f * buf[k]) * (hsc[d] * hsc[e2]);
+          }
+          if (k < P + N) return (kNegHalfLog2eH * -2.0f) * tA[k - P] * hsc[k - P];
+          if (k == P + N) return kNegHalfLog2eH * cst;
+          return 0.0f;
+        };
         float mx = 0.0f;
 #pragma unroll
-        for (int k = 0; k < P + N + 1; ++k) mx = fmaxf(mx, fabsf(coef[k]));
-        float back = 1.0f;
+        for (int k = 0; k < P + N + 1; ++k) mx = fmaxf(mx, fabsf(cf(k)));
+        float back = 1.0f, down = 1.0f;
         if (mx > kRowMax) {  // divide the row by 2^e, e = exponent(mx) - 13
           int e = (int)((__float_as_uint(mx) >> 23) & 0xffu) - 127 - 13;
           e = e > 120 ? 120 : e;
-          const float down = __uint_as_float((uint32_t)(127 - e) << 23);
+          down = __uint_as_float((uint32_t)(127 - e) << 23);
           back = __uint_as_float((uint32_t)(127 + e) << 23);
-#pragma unroll
-          for (int k = 0; k < KP; ++k) coef[k] *= down;
           scaled = true;
         }
-        store_row_h<KP>(st, st + S::B_BYTES, j, S::SBO, coef);
+#pragma unroll
+        for (int k = 0; k < KP; k += 8) {
+          uint4 h, l;
+          split_h2(cf(k) * down, cf(k + 1) * down, h.x, l.x);
+          split_h2(cf(k + 2) * down, cf(k + 3) * down, h.y, l.y);
+          split_h2(cf(k + 4) * down, cf(k + 5) * down, h.z, l.z);
+          split_h2(cf(k + 6) * down, cf(k + 7) * down, h.w, l.w);
+          const uint32_t off = kmajor_off_h(j, k, S::SBO);
+          *reinterpret_cast<uint4*>(st + off) = h;
+          *reinterpret_cast<uint4*>(st + S::B_BYTES + off) = l;
+        }
         float* wd = reinterpret_cast<float*>(st + 2 * S::B_BYTES) + (j >> 1) * 8 + (j & 1);
         wd[0] = buf[P + N];
         wd[2] = buf[P + N + 1];
@@ -302,8 +320,10 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
       if (lane == 0) sflag[s][warp] = any_scaled ? 1 : 0;
       fence_proxy_async();
       warp_arrive(&coef_full[s]);
+      if constexpr (PRE) {
 #pragma unroll
-      for (int k = 0; k < R4; ++k) cur[k] = nxt[k];
+        for (int k = 0; k < R4; ++k) cur[k] = nxt[k];
+      }
       // one decision per warp
       if (__shfl_sync(0xffffffffu, (!ok || *abort_flag) ? 1 : 0, 0)) break;
       if (warp == 3 && lane == 0) {
@@ -333,6 +353,10 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
         }
       }
       __syncwarp();
+      if constexpr (!PRE) {
+        load(g_next, cur);  // chunk i + 1
+        g_next = cand(i + 2);
+      }
     }
   } else {
     // ---- epilogue (tcgen05.ld 16x256b: thread t holds lanes t/4 and t/4 + 8
@@ -463,7 +487,7 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
 
 #define NDG_H_CASE(n, call) case n: call(n); break;
 
-int launch_fwd_h(int N, const FwdArgs& a, long long T, cudaStream_t s) {
+int launch_fwd_tc(int N, const FwdArgs& a, long long T, cudaStream_t s) {
   if (T <= 0) return 0;
 #define L_H(n)                                                                          \
   {                                                                                     \
@@ -474,6 +498,7 @@ int launch_fwd_h(int N, const FwdArgs& a, long long T, cudaStream_t s) {
   switch (N) {
     NDG_H_CASE(1, L_H) NDG_H_CASE(2, L_H) NDG_H_CASE(3, L_H) NDG_H_CASE(4, L_H)
     NDG_H_CASE(5, L_H) NDG_H_CASE(6, L_H) NDG_H_CASE(7, L_H) NDG_H_CASE(8, L_H)
+    NDG_H_CASE(9, L_H) NDG_H_CASE(10, L_H) NDG_H_CASE(11, L_H) NDG_H_CASE(12, L_H)
     default: return 0;
   }
 #undef L_H

@@ -112,11 +112,8 @@ int launch_cull_tile(int KP, const CullTileArgs& a, long long T, cudaStream_t s)
 int launch_permute_keys(const uint8_t* src, const int32_t* sorted, int n, int KP, uint8_t* dst,
                         cudaStream_t s);
 int launch_fwd(int N, const FwdArgs& a, long long T, cudaStream_t s);
-int launch_fwd_tc(int N, const FwdArgs& a, long long T, cudaStream_t s);
-int launch_fwd_h(int N, const FwdArgs& a, long long T, cudaStream_t s);  // N <= 8
-int launch_bwd_tc(int N, const BwdArgs& a, long long T, cudaStream_t s);  // N <= 6
+int launch_fwd_tc(int N, const FwdArgs& a, long long T, cudaStream_t s);  // FP16 hi/lo, N <= 12
 int launch_bwd_h(int N, const BwdArgs& a, long long T, cudaStream_t s);   // N <= 6
-size_t fwd_tc_smem(int N);
 int launch_loss(const float* y, const float* target, float* dy, long long n, double* part,
                  double* loss, cudaStream_t s);
 int launch_bwd(int N, const BwdArgs& a, long long T, cudaStream_t s);
