@@ -11,11 +11,11 @@
 // so after  S^T = Coef Phi^T  (MMA 1, candidates on the TMEM lanes) and
 // E = 2^S, one more product  D2 = E Psi  with  Psi[q, (c, k)] = dy_qc phi_qk
 // (built once per tile) yields all of them (MMA 2, A = E read straight from
-// tensor memory, B = Psi from shared memory).  Per entry the kernel then
-// forms the frame-free record [G = dl/dA (symmetric), v = Gc0 m~ - G_lin,
-// dl/dw] at the entry's Gaussian-major slot; both remaining factors are
-// linear with per-Gaussian matrices, dl/dM = 2 M sum G and dl/dm = 2 A sum v,
-// and are applied once per Gaussian after the segmented sum.
+// tensor memory, B = Psi from shared memory).  Per entry the kernel writes,
+// in entry order (BwdArgs::slot is not used), the frame-free record
+// [G = dl/dA (symmetric), v = Gc0 m~ - G_lin, dl/dw]; both remaining factors
+// are linear with per-Gaussian matrices, dl/dM = 2 M sum G and dl/dm = 2 A
+// sum v, and are applied once per Gaussian after the segmented sum.
 //
 // Operands are FP16 pairs v = hi + lo (three products).  Range: features are
 // scaled per tile and dimension into [-1, 1] (the coefficients take the
@@ -33,8 +33,8 @@
 //   warps 4-11  epilogue: warp w owns lanes 32 (w % 4) .. + 31 and columns
 //               64 ((w - 4) / 4) .. + 63 of each unit: e = 2^s written back in
 //               place as FP16 hi / lo (32 S columns -> 16 hi + 16 lo columns);
-//               warps of group (w - 4) / 4 also run the chain of every chunk i
-//               with i % 2 == group, one chunk behind.
+//               after each chunk both groups run the chain of the previous
+//               chunk, each writing its half of the entries' records.
 // Every wait is bounded; a timeout records NDG_ERR_TIMEOUT and the CTA lets
 // its issued MMAs finish (bounded) before it frees tensor memory.
 #include <cuda_fp16.h>
@@ -57,6 +57,10 @@ struct BwdHShape {
   static constexpr int R = rec_floats(N);   // record head: A, m, w
   static constexpr int R2 = rec_tc_floats(N);
   static constexpr int RP = part_floats(N);
+  static constexpr int RPT = RP;                       // per-entry record floats
+  static constexpr int RQT = RPT / 4;
+  static constexpr int SPLIT = (RPT / 2 + 3) / 4 * 4;  // record floats [0, SPLIT) by group 0
+  static constexpr int PQMAX = (SPLIT > RPT - SPLIT ? SPLIT : RPT - SPLIT) / 4;
   static constexpr int CS = 3;              // coefficient stages
   static constexpr uint32_t SBO_K = (KP / 8) * 128;   // rows of KP FP16 values
   static constexpr uint32_t SBO_Q = (256 / 8) * 128;  // Psi rows of 256 queries
@@ -64,16 +68,39 @@ struct BwdHShape {
   static constexpr uint32_t HALF_BYTES = 128u * KP * 2;
   static constexpr uint32_t PSI_BYTES = (uint32_t)NPSI * 256 * 2;
   static constexpr uint32_t C_BYTES = (uint32_t)NC * KP * 2;
-  static constexpr uint32_t STASH = 48;  // per candidate: m~ (N), w (3), slot, pad
+  static constexpr uint32_t STASH = 48;  // per candidate: m~ (N), w (3), live flag, pad
   static constexpr uint32_t C_STAGE = 2 * C_BYTES + NC * 4 + NC * STASH;  // hi, lo, row factors, stash
-  static constexpr uint32_t SMEM_USED = 2 * PHI_BYTES + 2 * PSI_BYTES + CS * C_STAGE + 128;
+  // per epilogue warp: its part of 16 records staged for coalesced stores
+  // (stride PQMAX + 1 float4 against bank conflicts)
+  static constexpr uint32_t OUT_BYTES = 16u * (PQMAX + 1) * 16;
+  static constexpr uint32_t SMEM_USED =
+      2 * PHI_BYTES + 2 * PSI_BYTES + CS * C_STAGE + 8 * OUT_BYTES + 128;
   static constexpr uint32_t SMEM = SMEM_USED > 116u * 1024u ? SMEM_USED : 116u * 1024u;
   static constexpr uint32_t TM_D2 = 256;
   static_assert(256 + 2 * NPSI <= 512, "tensor memory");
   static_assert(SMEM <= 227u * 1024u, "shared memory");
   static_assert(NPSI % 16 == 0 && NPSI <= 256, "MMA 2 shape");
-  static_assert(N + 4 <= 12, "stash");
+  static_assert(RPT >= P + N + 3 && N + 4 <= 12, "record / stash");
 };
+
+// Which lifted-coefficient gradients Gc_k (bit k) a group of the chain needs
+// for its record positions [p0, p1): G (i, k) needs Gc_ik, Gc_lin_i, Gc_lin_k
+// and Gc0; v_i needs Gc_lin_i and Gc0; dl/dw needs the constant column.
+template <int N>
+__host__ __device__ constexpr uint32_t chain_kmask(int p0, int p1) {
+  constexpr int P = tri(N);
+  uint32_t m = 0;
+  for (int d = 0; d < N; ++d)
+    for (int e = 0; e <= d; ++e) {
+      const int p = tri(d) + e;
+      if (p >= p0 && p < p1) m |= (1u << p) | (1u << (P + d)) | (1u << (P + e)) | (1u << (P + N));
+    }
+  for (int i = 0; i < N; ++i)
+    if (P + i >= p0 && P + i < p1) m |= (1u << (P + i)) | (1u << (P + N));
+  for (int c = 0; c < 3; ++c)
+    if (P + N + c >= p0 && P + N + c < p1) m |= 1u << (P + N);
+  return m;
+}
 
 namespace {
 
@@ -115,7 +142,7 @@ template <int N>
 __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
   using S = BwdHShape<N>;
   constexpr int P = S::P, F = S::F, KP = S::KP, NC = S::NC, NPSI = S::NPSI, CS = S::CS;
-  constexpr int R4 = S::R / 4, R2 = S::R2, RP = S::RP;
+  constexpr int R4 = S::R / 4, R2 = S::R2;
   extern __shared__ __align__(128) uint8_t dsm[];
   uint8_t* base = (uint8_t*)(((uintptr_t)dsm + 127) & ~(uintptr_t)127);
   uint8_t* PhiH = base;
@@ -123,6 +150,7 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
   uint8_t* PsiH = PhiL + S::PHI_BYTES;
   uint8_t* PsiL = PsiH + S::PSI_BYTES;
   uint8_t* Cst = PsiL + S::PSI_BYTES;  // CS stages of (hi, lo, row factors)
+  float4* Outs = reinterpret_cast<float4*>(Cst + CS * S::C_STAGE);  // 8 x OUT_BYTES
   __shared__ uint64_t coef_full[CS], coef_empty[CS], s_full[2], e_full[2], d2_full[2], d2_empty[2],
       drain;
   __shared__ uint32_t tmem_base;
@@ -139,13 +167,13 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
   if (tid == 0) {
     for (int i = 0; i < CS; ++i) {
       mbar_init(&coef_full[i], 4);
-      mbar_init(&coef_empty[i], 1 + 8 + 4);  // MMA 1, epilogue warps, chain warps
+      mbar_init(&coef_empty[i], 1 + 8 + 8);  // MMA 1, epilogue warps, chain warps
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&s_full[i], 1);
       mbar_init(&e_full[i], 8);
       mbar_init(&d2_full[i], 1);
-      mbar_init(&d2_empty[i], 4);
+      mbar_init(&d2_empty[i], 8);
     }
     mbar_init(&drain, 1);
     s_abort = 0;
@@ -252,13 +280,13 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
     float hsc[N];
 #pragma unroll
     for (int d = 0; d < N; ++d) hsc[d] = sh[d];
-    // candidate j of chunk i: Gaussian index (or -1) and output slot
+    // candidate j of chunk i: Gaussian index (or -1) and its entry index (or -1)
     auto cand = [&](int i) -> int2 {
       const long long e = beg + (long long)i * NC + j;
       const bool in = i < nchunks && e < end;
       const int g = in ? a.ids[e] : -1;
       const bool live = (unsigned)g < (unsigned)a.Ge;
-      const int sl = live ? (a.slot ? a.slot[e] : (int)e) : -1;
+      const int sl = live ? (int)e : -1;
       return make_int2(live ? g : -1, sl);
     };
     auto load = [&](int g, float4 (&r)[R4]) {
@@ -317,7 +345,7 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
       store_row_hb<KP>(st, st + S::C_BYTES, j, S::SBO_K, coef);
       reinterpret_cast<float*>(st + 2 * S::C_BYTES)[j] = back;
       {
-        // what the chain of this entry needs: m~, w and the output slot
+        // what the chain of this entry needs: m~, w and whether it is live
         float sv[12];
 #pragma unroll
         for (int d = 0; d < N; ++d) sv[d] = mt[d];
@@ -419,78 +447,119 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
     float hsc[N];
 #pragma unroll
     for (int d = 0; d < N; ++d) hsc[d] = sh[d];
-    // Chain of entry (candidate j, chunk ic): from D2 = sum_q e dy' phi' the
-    // lifted-coefficient gradient Gc, then the frame-free record
-    // [G = dl/dA (symmetric, lower packed), v = Gc0 m~ - G_lin, dl/dw];
-    // dl/dM = 2 M sum G and dl/dm = 2 A sum v follow per Gaussian.
-    auto chain = [&](int ic) -> bool {
+    // Chain of entry (candidate j, chunk ic), split between the two groups by
+    // record position.  From D2 = sum_q e dy' phi' the gradient with respect
+    // to the unscaled lifted coefficients is Gc_k = -1/2 h_k dys sum_c w_c
+    // D2[c][k] and dl/dw_c = dys D2[c][P + N] (the constant feature); the
+    // record is the frame-free [G = dl/dA (symmetric, lower packed), v = Gc0 m~
+    // - G_lin, dl/dw] (dl/dM = 2 M sum G and dl/dm = 2 A sum v follow per
+    // Gaussian).  Group g writes positions [g SPLIT, ...).
+    auto chain = [&](int ic, auto gtag) -> bool {
+      constexpr int GG = decltype(gtag)::value;
+      constexpr int RPT = S::RPT, SPLIT = S::SPLIT;
+      constexpr int p0 = GG ? SPLIT : 0, p1 = GG ? RPT : SPLIT, PW = p1 - p0, PQ = PW / 4;
       const int db = ic & 1, s = ic % CS;
-      const float4* stp = reinterpret_cast<const float4*>(Cst + s * S::C_STAGE + 2 * S::C_BYTES +
-                                                          NC * 4 + (uint32_t)j * S::STASH);
       float sv[12];
       {
+        const float4* stp = reinterpret_cast<const float4*>(Cst + s * S::C_STAGE + 2 * S::C_BYTES +
+                                                            NC * 4 + (uint32_t)j * S::STASH);
         const float4 v0 = stp[0], v1 = stp[1], v2 = stp[2];
         sv[0] = v0.x; sv[1] = v0.y; sv[2] = v0.z; sv[3] = v0.w;
         sv[4] = v1.x; sv[5] = v1.y; sv[6] = v1.z; sv[7] = v1.w;
         sv[8] = v2.x; sv[9] = v2.y; sv[10] = v2.z; sv[11] = v2.w;
       }
       warp_arrive(&coef_empty[s]);
-      const int slot = __float_as_int(sv[N + 3]);
+      const bool live = __float_as_int(sv[N + 3]) >= 0;
       if (!warp_wait(&d2_full[db], (ic >> 1) & 1, abort_flag)) return false;
       fence_after_sync();
-      // Gc_k = sum_c w_c D2[c][k], dl/dw_c = D2[c][P + N]
-      float Gc[F], gw[3];
+      constexpr uint32_t KM = chain_kmask<N>(p0, p1);  // needed Gc_k (F <= 28 bits)
+      float Gc[F], gw[3] = {0.f, 0.f, 0.f};
 #pragma unroll
       for (int k = 0; k < F; ++k) Gc[k] = 0.0f;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         uint32_t v[KP];
 #pragma unroll
-        for (int cb = 0; cb < KP; cb += 16)
-          tmem_ld16_nowait(tmem + lane_off + S::TM_D2 + (uint32_t)(db * NPSI + c * KP + cb), v + cb);
+        for (int b = 0; b < KP / 8; ++b)
+          if ((KM >> (8 * b)) & 0xffu)
+            tmem_ld8_nowait(tmem + lane_off + S::TM_D2 + (uint32_t)(db * NPSI + c * KP + 8 * b), v + 8 * b);
         tmem_wait_ld();
 #pragma unroll
-        for (int cb = 0; cb < KP; cb += 16) tmem_reg_fence16(v + cb);
+        for (int b = 0; b < KP / 8; ++b)
+          if ((KM >> (8 * b)) & 0xffu) tmem_reg_fence8(v + 8 * b);
         const float wc = sv[N + c];
 #pragma unroll
-        for (int k = 0; k < F; ++k) Gc[k] = fmaf(wc, __uint_as_float(v[k]), Gc[k]);
+        for (int k = 0; k < F; ++k)
+          if ((KM >> k) & 1u) Gc[k] = fmaf(wc, __uint_as_float(v[k]), Gc[k]);
         gw[c] = __uint_as_float(v[P + N]);
       }
       fence_before_sync();
       warp_arrive(&d2_empty[db]);
-      if (slot < 0) return true;
-      // back to the unscaled features and dy (Psi held dy / dys):
-      // Gc = -1/2 h_k dys sum_c w_c D2
       const float gsc = -0.5f * s_dys;
 #pragma unroll
       for (int d = 0; d < N; ++d)
 #pragma unroll
-        for (int k = 0; k <= d; ++k) Gc[tri(d) + k] *= gsc * (hsc[d] * hsc[k]);
+        for (int e = 0; e <= d; ++e)
+          if ((KM >> (tri(d) + e)) & 1u) Gc[tri(d) + e] *= gsc * (hsc[d] * hsc[e]);
 #pragma unroll
-      for (int d = 0; d < N; ++d) Gc[P + d] *= gsc * hsc[d];
+      for (int d = 0; d < N; ++d)
+        if ((KM >> (P + d)) & 1u) Gc[P + d] *= gsc * hsc[d];
       Gc[P + N] *= gsc;
       const float Gc0 = Gc[P + N];
-      float rec[RP];
+      float val[PW];
 #pragma unroll
-      for (int i = 0; i < N; ++i)
+      for (int k = 0; k < PW; ++k) val[k] = 0.0f;
 #pragma unroll
-        for (int k = 0; k <= i; ++k) {
-          const float mi = sv[i], mk = sv[k];
-          rec[tri(i) + k] =
-              (i == k) ? Gc[tri(i) + i] - 2.0f * Gc[P + i] * mi + Gc0 * mi * mi
-                       : Gc[tri(i) + k] - (Gc[P + i] * mk + Gc[P + k] * mi) + Gc0 * mi * mk;
+      for (int d = 0; d < N; ++d)
+#pragma unroll
+        for (int e = 0; e <= d; ++e) {
+          const int p = tri(d) + e;
+          if (p >= p0 && p < p1) {
+            const float mi = sv[d], mk = sv[e];
+            val[p - p0] = (d == e) ? Gc[p] - 2.0f * Gc[P + d] * mi + Gc0 * mi * mi
+                                   : Gc[p] - (Gc[P + d] * mk + Gc[P + e] * mi) + Gc0 * mi * mk;
+          }
         }
 #pragma unroll
-      for (int i = 0; i < N; ++i) rec[P + i] = Gc0 * sv[i] - Gc[P + i];
+      for (int i = 0; i < N; ++i)
+        if (P + i >= p0 && P + i < p1) val[P + i - p0] = Gc0 * sv[i] - Gc[P + i];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) rec[P + N + c] = gw[c] * s_dys;
+      for (int c = 0; c < 3; ++c)
+        if (P + N + c >= p0 && P + N + c < p1) val[P + N + c - p0] = gw[c] * s_dys;
+      if (!live) {
 #pragma unroll
-      for (int k = P + N + 3; k < RP; ++k) rec[k] = 0.0f;
-      float* out = a.part + (size_t)slot * RP;
+        for (int k = 0; k < PW; ++k) val[k] = 0.0f;
+      }
+      // The warp's 32 records are consecutive entries: stage this group's
+      // part of 16 records at a time and store with coalesced accesses;
+      // entries past the tile's end are not written.
+      const long long w0 = beg + (long long)ic * NC + quad * 32;
+      const long long nval = end - w0 < 32 ? end - w0 : 32;
+      float4* stg = Outs + (warp - 4) * (16 * (S::PQMAX + 1));
+      float4* dst = reinterpret_cast<float4*>(a.part) + w0 * S::RQT + p0 / 4;
 #pragma unroll
-      for (int k = 0; k < RP; k += 4)
-        *reinterpret_cast<float4*>(out + k) = make_float4(rec[k], rec[k + 1], rec[k + 2], rec[k + 3]);
+      for (int hb = 0; hb < 2; ++hb) {
+        if ((lane >> 4) == hb) {
+          const int r = lane & 15;
+#pragma unroll
+          for (int k = 0; k < PQ; ++k)
+            stg[r * (S::PQMAX + 1) + k] =
+                make_float4(val[4 * k], val[4 * k + 1], val[4 * k + 2], val[4 * k + 3]);
+        }
+        __syncwarp();
+        const int nrec = (int)(nval - 16 * hb < 0 ? 0 : (nval - 16 * hb < 16 ? nval - 16 * hb : 16));
+#pragma unroll
+        for (int m = 0; m < (16 * PQ + 31) / 32; ++m) {
+          const int idx = m * 32 + lane;
+          const int r = idx / PQ, k = idx - r * PQ;
+          if (r < nrec) dst[(long long)(16 * hb + r) * S::RQT + k] = stg[r * (S::PQMAX + 1) + k];
+        }
+        __syncwarp();
+      }
       return true;
+    };
+    auto chain_g = [&](int ic) -> bool {
+      return grp == 0 ? chain(ic, IntTag<0>{}) : chain(ic, IntTag<1>{});
     };
     float back = 1.0f;
     bool ok = true;
@@ -528,9 +597,9 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
       tmem_wait_st();
       fence_before_sync();
       warp_arrive(&e_full[sb]);
-      // chain of the previous chunk, by the group of its parity
-      if (h == nh - 1 && i >= 1 && ((i - 1) & 1) == grp) {
-        ok = chain(i - 1);
+      // chain of the previous chunk (both groups, each its half of the records)
+      if (h == nh - 1 && i >= 1) {
+        ok = chain_g(i - 1);
         if (!ok) break;
       }
       if (__shfl_sync(0xffffffffu, *abort_flag ? 1 : 0, 0)) {
@@ -538,7 +607,7 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
         break;
       }
     }
-    if (ok && nchunks >= 1 && ((nchunks - 1) & 1) == grp) ok = chain(nchunks - 1);
+    if (ok && nchunks >= 1) ok = chain_g(nchunks - 1);
     if (!ok && lane == 0) fail();
   }
   fence_before_sync();

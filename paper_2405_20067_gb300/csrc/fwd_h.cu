@@ -275,22 +275,32 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
           tA[d] = s2;
           cst = fmaf(mt[d], s2, cst);
         }
-        // coefficient k (compile-time after unrolling): quadratic (d, e),
-        // linear d, constant, zero padding
-        auto cf = [&](int k) -> float {
-          if (k < P) {
-            int d = 0;
-            while (tri(d + 1) <= k) ++d;
-            const int e2 = k - tri(d);
-            return kNegHalfLog2eH * (d == e2 ? buf[k] : 2.0f * buf[k]) * (hsc[d] * hsc[e2]);
-          }
-          if (k < P + N) return (kNegHalfLog2eH * -2.0f) * tA[k - P] * hsc[k - P];
-          if (k == P + N) return kNegHalfLog2eH * cst;
-          return 0.0f;
+        // coefficients kb .. kb + 7 (kb compile-time after unrolling):
+        // quadratic (d, e), linear d, constant, zero padding
+        auto cblock = [&](int kb, float (&v)[8]) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) v[q] = 0.0f;
+#pragma unroll
+          for (int d = 0; d < N; ++d)
+#pragma unroll
+            for (int e2 = 0; e2 <= d; ++e2) {
+              const int p = tri(d) + e2;
+              if (p >= kb && p < kb + 8)
+                v[p - kb] = kNegHalfLog2eH * (d == e2 ? buf[p] : 2.0f * buf[p]) * (hsc[d] * hsc[e2]);
+            }
+#pragma unroll
+          for (int d = 0; d < N; ++d)
+            if (P + d >= kb && P + d < kb + 8) v[P + d - kb] = (kNegHalfLog2eH * -2.0f) * tA[d] * hsc[d];
+          if (P + N >= kb && P + N < kb + 8) v[P + N - kb] = kNegHalfLog2eH * cst;
         };
         float mx = 0.0f;
 #pragma unroll
-        for (int k = 0; k < P + N + 1; ++k) mx = fmaxf(mx, fabsf(cf(k)));
+        for (int kb = 0; kb < KP; kb += 8) {
+          float v[8];
+          cblock(kb, v);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) mx = fmaxf(mx, fabsf(v[q]));
+        }
         float back = 1.0f, down = 1.0f;
         if (mx > kRowMax) {  // divide the row by 2^e, e = exponent(mx) - 13
           int e = (int)((__float_as_uint(mx) >> 23) & 0xffu) - 127 - 13;
@@ -300,13 +310,15 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
           scaled = true;
         }
 #pragma unroll
-        for (int k = 0; k < KP; k += 8) {
+        for (int kb = 0; kb < KP; kb += 8) {
+          float v[8];
+          cblock(kb, v);
           uint4 h, l;
-          split_h2(cf(k) * down, cf(k + 1) * down, h.x, l.x);
-          split_h2(cf(k + 2) * down, cf(k + 3) * down, h.y, l.y);
-          split_h2(cf(k + 4) * down, cf(k + 5) * down, h.z, l.z);
-          split_h2(cf(k + 6) * down, cf(k + 7) * down, h.w, l.w);
-          const uint32_t off = kmajor_off_h(j, k, S::SBO);
+          split_h2(v[0] * down, v[1] * down, h.x, l.x);
+          split_h2(v[2] * down, v[3] * down, h.y, l.y);
+          split_h2(v[4] * down, v[5] * down, h.z, l.z);
+          split_h2(v[6] * down, v[7] * down, h.w, l.w);
+          const uint32_t off = kmajor_off_h(j, kb, S::SBO);
           *reinterpret_cast<uint4*>(st + off) = h;
           *reinterpret_cast<uint4*>(st + S::B_BYTES + off) = l;
         }
