@@ -292,7 +292,7 @@ def run_reference(args):
 
 
 def run_fit(form: str, steps: int, warmup: int, device: str, flush, world: int, e2e_steps: int,
-            bwd_form: str | None = None):
+            bwd_form: str | None = None, graph: bool = False):
     """Times `steps` fit steps of the workload in one form ("tc": lifted
     tensor-core forward; "fp32": plain FP32 forward); backward, cull, loss,
     Adam and the refinement check are shared."""
@@ -315,9 +315,21 @@ def run_fit(form: str, steps: int, warmup: int, device: str, flush, world: int, 
         one_step(None)
     torch.cuda.synchronize()
     tr.check()
+    # per-kernel times and launch counts: traced eager steps (CUDA events
+    # around each call's main kernel on the launching stream)
+    ntr = max(3, steps // 4)
+    traces = [{n: ndg.Trace() for n in names} for _ in range(ntr)]
+    for i in range(ntr):
+        flush.zero_()
+        one_step(traces[i])
+    torch.cuda.synchronize()
+    kern = {n: statistics.mean(tr_[n].ms() for tr_ in traces) for n in names}
+    launches_per_step = sum(tr_[n].launches for tr_ in traces for n in names) / ntr
+    # the timed steps: the whole step captured once as a CUDA graph and replayed
+    if graph:
+        tr.capture(refine_each_step=True)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    traces = [{n: ndg.Trace() for n in names} for _ in range(steps)]
     pairs = []
     if world > 1:
         dist.barrier()
@@ -326,7 +338,10 @@ def run_fit(form: str, steps: int, warmup: int, device: str, flush, world: int, 
         for i in range(steps):
             flush.zero_()
             starts[i].record()
-            one_step(traces[i])
+            if graph:
+                tr.replay()
+            else:
+                one_step(None)
             ends[i].record()
             torch.cuda.synchronize()
             pairs.append(pairs_of(tr.ev.cull, Q, TILE))  # counted outside the timed region
@@ -340,11 +355,10 @@ def run_fit(form: str, steps: int, warmup: int, device: str, flush, world: int, 
         t = torch.tensor([total_ms], device=device)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    kern = {n: statistics.mean(tr_[n].ms() for tr_ in traces) for n in names}
-    launches = sum(tr_[n].launches for tr_ in traces for n in names)
     res = {"value": sum(pairs) * world / (total_ms / 1e3), "ms_per_step": total_ms / steps,
            "pairs_per_step": statistics.mean(pairs), "candidates_per_step": int(tr.ev.cull.E()),
-           "kernels_ms": kern, "gpu_launches": launches, "clocks": clk.summary()}
+           "kernels_ms": kern, "gpu_launches": int(round(launches_per_step * steps)),
+           "graph": graph, "clocks": clk.summary()}
     if e2e_steps:
         xh = x.cpu().pin_memory()
         th = target.cpu().pin_memory()
@@ -377,6 +391,8 @@ def main():
                     help="skip timing the plain FP32 form next to the chosen form")
     ap.add_argument("--bwd-form", default="tc", choices=["fp32", "tc"],
                     help="backward of the chosen form (its forward is the tensor-core one)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time eager steps instead of replays of the CUDA-graph-captured step")
     ap.add_argument("--workload", default="fit_n6", choices=sorted(WORKLOADS),
                     help="fit_n6: the headline workload; small_n6: 1/8 of it for profiling")
     args = ap.parse_args()
@@ -399,7 +415,7 @@ def main():
     peaks, peak_kind = load_peaks()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)  # > 129 MB L2
     chosen = run_fit("tc", args.steps, args.warmup, device, flush, world,
-                     max(3, args.steps // 2), bwd_form=args.bwd_form)
+                     max(3, args.steps // 2), bwd_form=args.bwd_form, graph=not args.no_graph)
     plain = None
     if not args.no_fp32_form:
         plain = run_fit("fp32", max(3, args.steps // 2), 3, device, flush, world, 0)
@@ -449,6 +465,8 @@ def main():
            "data": "synthetic",
            "config": {"workload": workload_name(G, Q),
                       "form": f"tensor-core forward + {args.bwd_form} backward",
+                      "step": ("one CUDA graph replay (cull, forward, loss, backward, Adam, "
+                               "refinement launches)" if chosen["graph"] else "eager launches"),
                       "pairs_per_step": mean_pairs,
                       "candidates_per_step": chosen["candidates_per_step"],
                       "l2": "256 MB buffer written between timed steps (untimed)",

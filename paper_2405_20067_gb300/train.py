@@ -94,6 +94,7 @@ class Trainer:
         self.noise = torch.randn(mix.G_cap, P + mix.N + 4, device=dev, generator=gen)
         self.iteration = 0
         self.traces = None
+        self.graph = None
 
     def set_traces(self, traces: dict | None):
         """traces: dict name -> ndg.Trace for build_cull / forward / loss /
@@ -140,6 +141,40 @@ class Trainer:
             refine = self.phase > 0 and self.iteration % self.phase == 0
         if refine:
             self.refine(sync=False)
+        return self.loss
+
+    def capture(self, refine_each_step: bool = True):
+        """Captures one whole step (cull, forward, loss, backward, Adam and,
+        with refine_each_step, the refinement launches) as a CUDA graph;
+        replay() runs it.  The graph reads the query and target buffers in
+        place (refill them with copy_ between replays); a change of the row
+        count G (check() after a materialising refinement) or of the
+        candidate capacity needs a new capture.  Two warm-up steps run on a
+        side stream first, as CUDA-graph capture of autograd requires."""
+        self.set_traces(None)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(2):
+                self._step_body(refine_each_step)
+        torch.cuda.current_stream().wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self._step_body(refine_each_step)
+        self.graph = g
+        return g
+
+    def _step_body(self, refine: bool):
+        self.step(refine=False)
+        if refine:
+            self.refine(sync=False)
+
+    def replay(self) -> torch.Tensor:
+        """One captured step; returns the (device) loss buffer."""
+        if self.graph is None:
+            raise RuntimeError("capture() first")
+        self.graph.replay()
+        self.iteration += 1
         return self.loss
 
     def _detached(self, mix):

@@ -68,3 +68,42 @@ def test_fit_reduces_loss_and_refines(ndg):
     assert tr.mix.has_children
     assert tr.mix.G >= G
     assert ndg.read_status(tr.ev.ws) == 0
+
+
+@pytest.mark.parametrize("mode", ["fp32", "tc"])
+def test_graph_replay_matches_eager_steps(ndg, mode):
+    """The CUDA-graph-captured step (cull, forward, loss, backward, Adam,
+    refinement launches) replayed K times leaves the parameters, moments and
+    loss bit-identical to K eager steps from the same state."""
+    import torch
+    from paper_2405_20067_gb300.train import Trainer, _PARAMS
+    N, G, Q = 6, 600, 8192
+    md = ndg.NDG_MODE_TC if mode == "tc" else ndg.NDG_MODE_FP32
+
+    def make():
+        mix = synth.mixture(N, G, 70)
+        ch = synth.children(N, G, 71, spread=0.05, brightness=(0.0009, 0.0011))
+        gm = ndg.Mixture.from_arrays(N, mix, ch, G_cap=2 * G)
+        x = torch.as_tensor(synth.queries_box(N, Q, 72)).cuda()
+        target = torch.as_tensor(synth.targets_uniform(Q, 73)).cuda()
+        cp = ndg.CullParams(8, torch.as_tensor(synth.projections(N, 8, 74)).cuda(), 1 / 255, 3.0, 64)
+        return Trainer(gm, x, target, 256, cp, lr=1e-3, t=0.01, phase=0, mode=md, seed=5)
+
+    a, b = make(), make()
+    # the capture's two warm-up steps are steps too: match them eagerly
+    for _ in range(2):
+        a.step(refine=False)
+        a.refine(sync=False)
+    b.capture(refine_each_step=True)
+    for _ in range(3):
+        a.step(refine=False)
+        a.refine(sync=False)
+        b.replay()
+    torch.cuda.synchronize()
+    assert a.check() == ndg.NDG_OK and b.check() == ndg.NDG_OK
+    assert torch.equal(a.loss, b.loss)
+    for f in _PARAMS:
+        pa, pb = getattr(a.mix, f), getattr(b.mix, f)
+        if pa is not None:
+            assert torch.equal(pa.detach(), pb.detach()), f
+            assert torch.equal(getattr(a.m1, f), getattr(b.m1, f)), f
