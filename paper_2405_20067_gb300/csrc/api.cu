@@ -51,7 +51,7 @@ struct CullLayout {
       end;
 };
 struct BwdLayout {
-  size_t part, sk_a, sv_a, sk_b, sv_b, goff, gsum, tmp, end;
+  size_t part, sk_a, sv_a, sk_b, sv_b, goff, gsum, te, tmp, end;
 };
 
 CommonLayout common_layout(const Sizes& z) {
@@ -92,6 +92,9 @@ CullLayout cull_layout(const Sizes& z, size_t base) {
   return c;
 }
 
+// longest per-Gaussian segment (= tiles) the shared-memory segment sort takes
+constexpr long long kMaxSegSort = 32768;
+
 BwdLayout bwd_layout(const Sizes& z, size_t base) {
   Region r;
   r.off = base;
@@ -103,7 +106,11 @@ BwdLayout bwd_layout(const Sizes& z, size_t base) {
   b.sv_b = r.take((size_t)z.E_cap * 4);
   b.goff = r.take(((size_t)z.Ge_cap + 1) * sizeof(long long));
   b.gsum = r.take((size_t)z.Ge_cap * part_floats(z.N) * sizeof(float));
-  b.tmp = r.take(radix_temp_bytes(z.E_cap));
+  b.te = r.take((size_t)z.E_cap * sizeof(unsigned long long));
+  {
+    const size_t t1 = radix_temp_bytes(z.E_cap), t2 = transpose_temp_bytes(z.Ge_cap);
+    b.tmp = r.take(t1 > t2 ? t1 : t2);
+  }
   b.end = r.off;
   return b;
 }
@@ -393,17 +400,26 @@ ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q, const ndg_
   pa.rec_kind = mode == NDG_MODE_TC ? 2 : 0;
   pa.status = &reinterpret_cast<WsHeader*>(w + c.header)->status;
   tr += launch_prep(N, pa, s);
-  // Gaussian-major order of the entries (stable radix sort by Gaussian
-  // index): the per-entry partial records are written in entry order and
-  // summed per Gaussian through this permutation.
+  // Gaussian-major order of the entries (the stable order of a sort by
+  // Gaussian index): the per-entry partial records are written in entry
+  // order and summed per Gaussian through this permutation.  A Gaussian
+  // occurs at most once per tile, so segments are at most T long: a counting
+  // sort with per-segment sorts in shared memory when T fits, else a radix sort.
   const int Ge = pa.Ge;
-  uint32_t* sk;
   int32_t* sv;
-  tr += radix_sort_pairs((const uint32_t*)cull->ids, nullptr, (uint32_t*)(w + L.sk_a),
-                         (int32_t*)(w + L.sv_a), (uint32_t*)(w + L.sk_b), (int32_t*)(w + L.sv_b),
-                         cull->E_cap, cull->E_dev, bits_for(Ge > 0 ? Ge : 1), w + L.tmp, s, &sk, &sv);
   long long* goff = (long long*)(w + L.goff);
-  tr += bin_boundaries(sk, cull->E_cap, cull->E_dev, Ge, goff, s);
+  if (z.T <= kMaxSegSort) {
+    sv = (int32_t*)(w + L.sv_a);
+    tr += transpose_entries(cull->ids, cull->offsets, z.T, cull->E_cap, cull->E_dev, Ge, goff,
+                            (unsigned long long*)(w + L.te), sv, w + L.tmp, s);
+  } else {
+    uint32_t* sk;
+    tr += radix_sort_pairs((const uint32_t*)cull->ids, nullptr, (uint32_t*)(w + L.sk_a),
+                           (int32_t*)(w + L.sv_a), (uint32_t*)(w + L.sk_b), (int32_t*)(w + L.sv_b),
+                           cull->E_cap, cull->E_dev, bits_for(Ge > 0 ? Ge : 1), w + L.tmp, s, &sk,
+                           &sv);
+    tr += bin_boundaries(sk, cull->E_cap, cull->E_dev, Ge, goff, s);
+  }
   BwdArgs ba{};
   ba.x = q->x;
   ba.dy = dy;

@@ -31,4 +31,15 @@ int radix_sort_pairs(const uint32_t* keys_in, const int32_t* vals_in, uint32_t* 
 int bin_boundaries(const uint32_t* sorted, long long n_cap, const long long* n_dev,
                     int nbins, long long* off, cudaStream_t s);
 
+// Gaussian-major order of candidate entries: goff[0..nid] segment offsets
+// and perm[goff[g] .. goff[g+1]) the entries with id g in ascending order
+// (the stable order of a sort by id).  Every id must occur at most once per
+// tile (offsets [T+1] delimit the tiles' entries); te [n_cap] is scratch for
+// (tile, entry) pairs; tr_rank uses T / 4 bytes of shared memory per warp
+// (T <= 32768: 64 KB per block).
+size_t transpose_temp_bytes(int nid);
+int transpose_entries(const int32_t* ids, const long long* offsets, long long T, long long n_cap,
+                      const long long* n_dev, int nid, long long* goff, unsigned long long* te,
+                      int32_t* perm, void* temp, cudaStream_t s);
+
 }  // namespace ndg

@@ -283,4 +283,126 @@ int bin_boundaries(const uint32_t* sorted, long long n_cap, const long long* n_d
   return 1;
 }
 
+// ---- Gaussian-major order of candidate entries -------------------------------
+// A stable counting sort of the entries by id, using that an id occurs at
+// most once per tile (so the stable order of an id's entries is their tile
+// order): per-id counts (atomics), exclusive scan (goff), scatter of
+// (tile, entry) through per-id cursors (atomics: arbitrary order inside a
+// segment), then per segment (one warp) a bitmap of its tiles in shared
+// memory: an entry's rank is the number of set bits below its tile.
+__global__ void tr_count(const int32_t* __restrict__ ids, long long n_cap,
+                         const long long* __restrict__ n_dev, int nid,
+                         unsigned long long* __restrict__ cnt) {
+  const long long n = rs_count(n_cap, n_dev);
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int g = ids[e];
+    if ((unsigned)g < (unsigned)nid) atomicAdd(cnt + g, 1ull);
+  }
+}
+
+// One block per tile: its entries [offsets[t], offsets[t+1]).
+__global__ void __launch_bounds__(256) tr_scatter(const long long* __restrict__ offsets,
+                                                  const int32_t* __restrict__ ids, int nid,
+                                                  unsigned long long* __restrict__ cur,
+                                                  unsigned long long* __restrict__ te) {
+  const long long t = blockIdx.x;
+  const long long b = offsets[t], en = offsets[t + 1];
+  for (long long e = b + threadIdx.x; e < en; e += blockDim.x) {
+    const int g = ids[e];
+    if ((unsigned)g < (unsigned)nid)
+      te[atomicAdd(cur + g, 1ull)] = ((unsigned long long)t << 32) | (unsigned long long)e;
+  }
+}
+
+// One warp per segment (persistent over segments); words = ceil(T / 32).
+__global__ void __launch_bounds__(256) tr_rank(const long long* __restrict__ goff, int nid,
+                                               const unsigned long long* __restrict__ te,
+                                               int words, int32_t* __restrict__ perm) {
+  extern __shared__ uint32_t tsm[];  // per warp: bitmap [words], prefix [words]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* bm = tsm + (size_t)warp * 2 * words;
+  uint32_t* pre = bm + words;
+  for (int g = blockIdx.x * 8 + warp; g < nid; g += gridDim.x * 8) {
+    const long long b = goff[g];
+    const int L = (int)(goff[g + 1] - b);
+    if (L == 0) continue;
+    if (L == 1) {
+      if (lane == 0) perm[b] = (int32_t)(te[b] & 0xffffffffull);
+      continue;
+    }
+    // tile span of the segment: only those bitmap words are touched
+    for (int w = lane; w < words; w += 32) bm[w] = 0u;
+    __syncwarp();
+    for (int i = lane; i < L; i += 32) {
+      const uint32_t t = (uint32_t)(te[b + i] >> 32);
+      atomicOr(bm + (t >> 5), 1u << (t & 31));
+    }
+    __syncwarp();
+    // exclusive prefix of the words' popcounts (lane-sequential chunks + warp scan)
+    const int per = (words + 31) / 32;
+    int run = 0;
+    for (int k = 0; k < per; ++k) {
+      const int w = lane * per + k;
+      if (w < words) run += __popc(bm[w]);
+    }
+    int incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    int acc = incl - run;
+    for (int k = 0; k < per; ++k) {
+      const int w = lane * per + k;
+      if (w < words) {
+        pre[w] = (uint32_t)acc;
+        acc += __popc(bm[w]);
+      }
+    }
+    __syncwarp();
+    for (int i = lane; i < L; i += 32) {
+      const unsigned long long v = te[b + i];
+      const uint32_t t = (uint32_t)(v >> 32);
+      const int r = (int)pre[t >> 5] + __popc(bm[t >> 5] & ((1u << (t & 31)) - 1u));
+      perm[b + r] = (int32_t)(v & 0xffffffffull);
+    }
+    __syncwarp();
+  }
+}
+
+size_t transpose_temp_bytes(int nid) {
+  const size_t c = ((size_t)(nid > 0 ? nid : 1) * sizeof(unsigned long long) + 255) / 256 * 256;
+  return c + scan_temp_bytes(nid > 0 ? nid : 1);
+}
+
+int transpose_entries(const int32_t* ids, const long long* offsets, long long T, long long n_cap,
+                      const long long* n_dev, int nid, long long* goff, unsigned long long* te,
+                      int32_t* perm, void* temp, cudaStream_t s) {
+  const size_t c = ((size_t)(nid > 0 ? nid : 1) * sizeof(unsigned long long) + 255) / 256 * 256;
+  unsigned long long* cnt = (unsigned long long*)temp;
+  void* stemp = (char*)temp + c;
+  cudaMemsetAsync(cnt, 0, (size_t)(nid > 0 ? nid : 1) * sizeof(unsigned long long), s);
+  long long blocks = ceil_div<long long>(n_cap > 0 ? n_cap : 1, 256);
+  if (blocks > 4 * 1024) blocks = 4 * 1024;
+  tr_count<<<(unsigned)blocks, 256, 0, s>>>(ids, n_cap, n_dev, nid, cnt);
+  int launched = 1 + scan_exclusive_i64((const long long*)cnt, goff, nid, stemp, s);
+  // the counts become the cursors: cur[g] = goff[g]
+  cudaMemcpyAsync(cnt, goff, (size_t)nid * sizeof(long long), cudaMemcpyDeviceToDevice, s);
+  if (T > 0) {
+    tr_scatter<<<(unsigned)T, 256, 0, s>>>(offsets, ids, nid, cnt, te);
+    ++launched;
+  }
+  if (nid > 0) {
+    const int words = (int)((T + 31) / 32 > 0 ? (T + 31) / 32 : 1);
+    const size_t smem = (size_t)8 * 2 * words * sizeof(uint32_t);
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(tr_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int rb = ceil_div(nid, 8) < 152 * 8 ? ceil_div(nid, 8) : 152 * 8;
+    tr_rank<<<(unsigned)rb, 256, smem, s>>>(goff, nid, te, words, perm);
+    ++launched;
+  }
+  return launched;
+}
+
 }  // namespace ndg
