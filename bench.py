@@ -266,6 +266,23 @@ def cpu_baseline(c, ch, seconds: float = 15.0):
             "seconds": round(t, 2)}
 
 
+def max_over_ranks(v: float, world: int, device="cpu") -> float:
+    """The largest of the ranks' values (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(pairs_per_rank: float, world: int, total_ms: float) -> float:
+    """Whole-job pairs/s of `world` independent replicas (weak scaling: every
+    rank evaluates the same workload), timed by the slowest rank."""
+    return pairs_per_rank * world / (total_ms / 1e3)
+
+
 def run_reference(args):
     """The oracle as it stands, timed on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -350,12 +367,8 @@ def run_fit(form: str, steps: int, warmup: int, device: str, flush, world: int, 
         dist.barrier()
     st = tr.check()
     assert st == ndg.NDG_OK, ndg.status_string(st)
-    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    if world > 1:
-        t = torch.tensor([total_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    res = {"value": sum(pairs) * world / (total_ms / 1e3), "ms_per_step": total_ms / steps,
+    total_ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), world, device)
+    res = {"value": job_throughput(sum(pairs), world, total_ms), "ms_per_step": total_ms / steps,
            "pairs_per_step": statistics.mean(pairs), "candidates_per_step": int(tr.ev.cull.E()),
            "kernels_ms": kern, "gpu_launches": int(round(launches_per_step * steps)),
            "graph": graph, "clocks": clk.summary()}
