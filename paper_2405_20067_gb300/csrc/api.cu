@@ -47,8 +47,8 @@ struct CommonLayout {
   size_t header, rec, loss, dflag, drank, dfresh, end;
 };
 struct CullLayout {
-  size_t tb, range, tkey, gkey, gkey_sorted, bin, bk_a, bv_a, bk_b, bv_b, binoff, counts, excl, tmp,
-      end;
+  size_t tb, range, tkey, gkey, gkey_sorted, bin, bk_a, bv_a, bk_b, bv_b, binoff, counts, excl, masks,
+      tmp, end;
 };
 struct BwdLayout {
   size_t part, sk_a, sv_a, sk_b, sv_b, goff, gsum, te, tmp, end;
@@ -66,6 +66,8 @@ CommonLayout common_layout(const Sizes& z) {
   c.end = r.off;
   return c;
 }
+
+long long mask_words(const Sizes& z) { return ((long long)z.Ge_cap + 31) / 32 + 8; }
 
 CullLayout cull_layout(const Sizes& z, size_t base) {
   Region r;
@@ -86,6 +88,8 @@ CullLayout cull_layout(const Sizes& z, size_t base) {
   // per (tile, warp slice) survivor counts and their exclusive scan
   c.counts = r.take((size_t)(8 * z.T + 1) * sizeof(long long));
   c.excl = r.take((size_t)(8 * z.T + 1) * sizeof(long long));
+  // survivor ballots: a tile visits each Gaussian at most once
+  c.masks = r.take((size_t)(z.T > 0 ? z.T : 1) * mask_words(z) * sizeof(uint32_t));
   size_t t1 = radix_temp_bytes(z.Ge_cap), t2 = scan_temp_bytes(8 * z.T + 1);
   c.tmp = r.take(t1 > t2 ? t1 : t2);
   c.end = r.off;
@@ -309,6 +313,8 @@ ndg_status ndg_build_cull(const ndg_mixture* mix, const ndg_queries* q, const nd
   ca.excl = nullptr;
   ca.ids = nullptr;
   ca.E_cap = out->E_cap;
+  ca.masks = (uint32_t*)(w + L.masks);
+  ca.mask_words = mask_words(z);
   tr += launch_cull_tile(KP, ca, T, s);
   long long* excl = (long long*)(w + L.excl);
   tr += scan_exclusive_i64(ca.counts, excl, 8 * T, w + L.tmp, s);

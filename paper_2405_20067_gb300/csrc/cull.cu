@@ -307,10 +307,12 @@ __device__ __forceinline__ bool keys_overlap(const uint32_t* glo, const uint32_t
 // One CTA of CT_WARPS warps per tile.  The tile's sources (Gaussians whose
 // first-projection bucket range meets the tile's) are thi0 + 1 runs of the
 // bin-sorted order; warp w takes the contiguous slice w of their
-// concatenation, walks it 32 elements at a time (each lane tracks its run),
-// tests the remaining projections and counts (count pass) or writes (fill
-// pass, at the scanned offset of (tile, warp)) the survivors in order, so the
-// list order is the concatenation order.
+// concatenation (slice bounds at multiples of 32), walks it 32 elements at
+// a time (each lane tracks its run).  The count pass tests the remaining
+// projections, counts the survivors and stores the ballot of every 32
+// sources in masks[t][i / 32]; the fill pass reads the ballots back (no
+// key loads) and writes the survivors in order at the scanned offset of
+// (tile, warp), so the list order is the concatenation order.
 template <int KP>
 __global__ void __launch_bounds__(256) cull_tile_kernel(CullTileArgs a) {
   constexpr int W = KP / 4;  // 32-bit words per key half (KP >= 8)
@@ -356,7 +358,12 @@ __global__ void __launch_bounds__(256) cull_tile_kernel(CullTileArgs a) {
     __syncthreads();
   }
   const long long n_src = s_total;
-  const long long lo = n_src * warp / 8, hi = n_src * (warp + 1) / 8;
+  auto bound = [&](int w) -> long long {
+    const long long v = (n_src * w / 8 + 31) / 32 * 32;
+    return v < n_src ? v : n_src;
+  };
+  const long long lo = bound(warp), hi = warp == 7 ? n_src : bound(warp + 1);
+  uint32_t* masks = a.masks + t * a.mask_words;
   // run of the slice's first element: largest r with rpre[r] <= lo
   int r = 0;
   {
@@ -372,27 +379,33 @@ __global__ void __launch_bounds__(256) cull_tile_kernel(CullTileArgs a) {
   long long count = 0;
   for (long long i0 = lo; i0 < hi; i0 += 32) {
     const long long i = i0 + lane;
-    bool pass = false;
-    int e = 0;
-    if (i < hi) {
-      while (r + 1 < nr && rpre[r + 1] <= i) ++r;
-      const long long pos = rbeg[r] + (i - rpre[r]);
-      e = a.sorted_ids[pos];
-      if (KP > 0) {
-        // keys in bin-sorted order: a warp reads consecutive rows
-        const uint32_t* gk = reinterpret_cast<const uint32_t*>(a.gkey + (size_t)pos * 2 * KP);
-        uint32_t glo[W > 0 ? W : 1], ghi[W > 0 ? W : 1];
+    unsigned bal;
+    if (!fill) {
+      bool pass = false;
+      if (i < hi) {
+        if (KP > 0) {
+          while (r + 1 < nr && rpre[r + 1] <= i) ++r;
+          const long long pos = rbeg[r] + (i - rpre[r]);
+          // keys in bin-sorted order: a warp reads consecutive rows
+          const uint32_t* gk = reinterpret_cast<const uint32_t*>(a.gkey + (size_t)pos * 2 * KP);
+          uint32_t glo[W > 0 ? W : 1], ghi[W > 0 ? W : 1];
 #pragma unroll
-        for (int w = 0; w < W; ++w) { glo[w] = gk[w]; ghi[w] = gk[W + w]; }
-        pass = keys_overlap(glo, ghi, tlo, thi, W);
-      } else {
-        pass = true;
+          for (int w = 0; w < W; ++w) { glo[w] = gk[w]; ghi[w] = gk[W + w]; }
+          pass = keys_overlap(glo, ghi, tlo, thi, W);
+        } else {
+          pass = true;
+        }
       }
-    }
-    const unsigned bal = __ballot_sync(0xffffffffu, pass);
-    if (fill && pass) {
-      const long long pos = written + count + __popc(bal & ((1u << lane) - 1u));
-      if (pos < a.E_cap) a.ids[pos] = e;
+      bal = __ballot_sync(0xffffffffu, pass);
+      if (lane == 0) masks[i0 >> 5] = bal;
+    } else {
+      bal = masks[i0 >> 5];
+      if ((bal >> lane) & 1u) {
+        while (r + 1 < nr && rpre[r + 1] <= i) ++r;
+        const long long src = rbeg[r] + (i - rpre[r]);
+        const long long pos = written + count + __popc(bal & ((1u << lane) - 1u));
+        if (pos < a.E_cap) a.ids[pos] = a.sorted_ids[src];
+      }
     }
     count += __popc(bal);
   }

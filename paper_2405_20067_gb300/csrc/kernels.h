@@ -33,6 +33,8 @@ struct CullTileArgs {
   const long long* excl;      // fill pass: exclusive scan of counts
   int* ids;                   // fill pass: [E_cap]
   long long E_cap;
+  uint32_t* masks;            // [T][mask_words] survivor ballots of the count pass
+  long long mask_words;       // per tile: >= ceil(max sources / 32) + 8
 };
 
 struct FwdArgs {
