@@ -17,24 +17,25 @@
 //     stage carries a flag so that chunks without such rows skip it).
 //
 // CTA = one tile of up to 256 queries (two M = 128 row blocks sharing the
-// candidate operand), 384 threads, one CTA per SM (it owns all 512 TMEM
+// candidate operand), 416 threads, one CTA per SM (it owns all 512 TMEM
 // columns: two accumulator buffers x two row blocks x 128 candidates):
 //   warps 0-3   builders: thread j turns candidate j of a chunk of 128 into
 //               its coefficient row (FP16 hi / lo, K-major no-swizzle layout)
 //               and weight pair entry in one of CS shared-memory stages; the
 //               records of the next chunk are loaded into registers meanwhile;
-//               each warp then arrives on coef_full.  The warps are coupled
-//               only through these barriers, so warps 0-2 may run ahead;
-//               lane 0 of warp 3 issues the MMAs of a chunk once its stage is
-//               full and accumulator buffer i & 1 is free, and commits them
-//               to acc_full and coef_empty;
-//   warps 4-11  epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of both
-//               row blocks (query rows r and r + 128), columns 64 ((w - 4) / 4)
-//               .. + 63 (half of the candidates), with the 16x256b load shape
-//               (a thread holds 8 rows x 8 columns of each 32-column block),
-//               forms e = 2^s and accumulates w e; partial row sums are
-//               combined with shuffles and, across the two column halves,
-//               through shared memory at the end.
+//               each warp then arrives on coef_full;
+//   warp 12     MMA issuer: lane 0 issues the MMAs of chunk i once its stage
+//               is full and accumulator buffer i & 1 is free, and commits
+//               them to acc_full and coef_empty (a warp of its own, so that
+//               issuing overlaps the building of the next chunks);
+//   warps 4-11  epilogue: warps 4-7 serve row block 0, warps 8-11 row block 1
+//               (each block has its own accumulator barriers, so the two
+//               groups run independently); warp w reads TMEM lanes 32 (w % 4)
+//               .. + 31 of its block at all 128 columns with the 16x256b load
+//               shape (a thread holds 4 rows x 2 columns of every 8-column
+//               group), the loads of the next 32 columns in flight while the
+//               current ones are used; it forms e = 2^s and accumulates w e;
+//               row sums are completed with shuffles at the end.
 // Barrier operations are one per warp (an elected lane), and every wait is
 // bounded: on a timeout the kernel records NDG_ERR_TIMEOUT, lets the issued
 // MMAs finish (bounded), frees its tensor memory and returns.
@@ -62,8 +63,7 @@ struct FwdHShape {
   static constexpr uint32_t B_BYTES = (uint32_t)NC * KP * 2;
   static constexpr uint32_t W_BYTES = (uint32_t)NC * 16;  // w0 w0' w1 w1' w2 w2' k k' per pair
   static constexpr uint32_t C_STAGE = 2 * B_BYTES + W_BYTES;
-  static constexpr uint32_t RED_BYTES = 256u * 4 * 4;      // column-half partial sums
-  static constexpr uint32_t SMEM_USED = 2 * PHI_BYTES + CS * C_STAGE + RED_BYTES + 128;
+  static constexpr uint32_t SMEM_USED = 2 * PHI_BYTES + CS * C_STAGE + 128;
   // more than half of the SM's shared memory: one CTA per SM
   static constexpr uint32_t SMEM = SMEM_USED > 116u * 1024u ? SMEM_USED : 116u * 1024u;
   static_assert(SMEM <= 227u * 1024u, "shared memory");
@@ -110,7 +110,7 @@ constexpr float kRowMax = 16384.0f;  // coefficient rows are kept below 2^14 (FP
 }  // namespace
 
 template <int N>
-__global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
+__global__ void __launch_bounds__(416, 1) fwd_h_kernel(FwdArgs a) {
   using S = FwdHShape<N>;
   constexpr int P = S::P, KP = S::KP, NC = S::NC, CS = S::CS, R = S::R, R4 = R / 4;
   extern __shared__ __align__(128) uint8_t dsm[];
@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
   uint8_t* Ahi = base;
   uint8_t* Alo = Ahi + S::PHI_BYTES;
   uint8_t* Cst = Alo + S::PHI_BYTES;  // CS stages of (Bhi, Blo, weights)
-  float* red = reinterpret_cast<float*>(Cst + CS * S::C_STAGE);
-  __shared__ uint64_t coef_full[CS], coef_empty[CS], acc_full[2], acc_empty[2], drain;
+  // accumulator barriers per (buffer, row block): index 2 b + h
+  __shared__ uint64_t coef_full[CS], coef_empty[CS], acc_full[4], acc_empty[4], drain;
   __shared__ uint32_t tmem_base;
   __shared__ float sred[8 * N * 2];
   __shared__ float sctr[N], sh[N];
@@ -136,11 +136,11 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
   if (tid == 0) {
     for (int i = 0; i < CS; ++i) {
       mbar_init(&coef_full[i], 4);
-      mbar_init(&coef_empty[i], 1 + 8);
+      mbar_init(&coef_empty[i], 1 + 4 * nh);  // issuer commit + the busy epilogue warps
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 4; ++i) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], 8);
+      mbar_init(&acc_empty[i], 4);
     }
     mbar_init(&drain, 1);
     s_abort = 0;
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
     tmem_relinquish();
   }
   const int row = tid - 128;  // epilogue threads: Phi row
-  const bool is_epi = warp >= 4;
+  const bool is_epi = warp >= 4 && warp < 12;
   const bool active_row = is_epi && row < nq;
   float xq[N];
 #pragma unroll
@@ -233,18 +233,13 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
         for (int k = 0; k < R4; ++k) r[k] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     };
-    // N <= 8: the records of chunk i + 1 are loaded into registers while
+    // N <= 6: the records of chunk i + 1 are loaded into registers while
     // chunk i is built; larger records are loaded right after a build (the
     // latency overlaps the next stage wait) to keep the register count down.
-    constexpr bool PRE = N <= 8;
+    constexpr bool PRE = N <= 6;
     float4 cur[R4], nxt[PRE ? R4 : 1];
     load(cand(0), cur);
     int g_next = cand(1);
-    // descriptor bases (a descriptor for base + off is base + off / 16)
-    const uint64_t dA0 = smem_desc(smem_u32(Ahi), 128, S::SBO);
-    const uint64_t dB0 = smem_desc(smem_u32(Cst), 128, S::SBO);
-    constexpr uint64_t A_LO = S::PHI_BYTES >> 4, B_LO = S::B_BYTES >> 4;
-    constexpr uint32_t IDESC = idesc_f16(NC);
     for (int i = 0; i < nchunks; ++i) {
       const int s = i % CS;
       if constexpr (PRE) {
@@ -338,54 +333,134 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
       }
       // one decision per warp
       if (__shfl_sync(0xffffffffu, (!ok || *abort_flag) ? 1 : 0, 0)) break;
-      if (warp == 3 && lane == 0) {
-        // MMA issue for chunk i: once all four builder warps have filled the
-        // stage and accumulator buffer i & 1 is free
-        const int b = i & 1;
-        bool ok2 = mbar_wait_sleep(&coef_full[s], (i / CS) & 1, abort_flag);
-        if (ok2 && i >= 2) ok2 = mbar_wait_sleep(&acc_empty[b], ((i >> 1) - 1) & 1, abort_flag);
-        if (!ok2) {
-          fail();
-        } else {
-          fence_after_sync();
-          const uint64_t dbh = dB0 + (uint64_t)((s * S::C_STAGE) >> 4);
-          for (int h = 0; h < nh; ++h) {
-            const uint32_t d = tmem + (uint32_t)(b * 256 + h * 128);
-            const uint64_t dah = dA0 + (uint64_t)((h * S::HALF_BYTES) >> 4);
-#pragma unroll
-            for (int ks = 0; ks < KP / 16; ++ks) {
-              const uint64_t ko = (uint64_t)ks * 16u;  // two 16-byte core matrices per K step
-              mma_f16(d, dah + ko, dbh + ko, IDESC, ks > 0 ? 1u : 0u);
-              mma_f16(d, dah + ko, dbh + B_LO + ko, IDESC, 1u);
-              mma_f16(d, dah + A_LO + ko, dbh + ko, IDESC, 1u);
-            }
-          }
-          mma_commit(&acc_full[b]);
-          mma_commit(&coef_empty[s]);
-        }
-      }
-      __syncwarp();
       if constexpr (!PRE) {
         load(g_next, cur);  // chunk i + 1
         g_next = cand(i + 2);
       }
     }
+  } else if (warp == 12) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      // descriptor bases (a descriptor for base + off is base + off / 16)
+      const uint64_t dA0 = smem_desc(smem_u32(Ahi), 128, S::SBO);
+      const uint64_t dB0 = smem_desc(smem_u32(Cst), 128, S::SBO);
+      constexpr uint64_t A_LO = S::PHI_BYTES >> 4, B_LO = S::B_BYTES >> 4;
+      constexpr uint32_t IDESC = idesc_f16(NC);
+      for (int i = 0; i < nchunks; ++i) {
+        const int s = i % CS, b = i & 1;
+        bool ok = mbar_wait_sleep(&coef_full[s], (i / CS) & 1, abort_flag);
+        const uint64_t dbh = dB0 + (uint64_t)((s * S::C_STAGE) >> 4);
+        for (int h = 0; ok && h < nh; ++h) {
+          // row block h of buffer b is free once its epilogue group has read chunk i - 2
+          if (i >= 2) ok = mbar_wait_sleep(&acc_empty[2 * b + h], ((i >> 1) - 1) & 1, abort_flag);
+          if (!ok) break;
+          fence_after_sync();
+          const uint32_t d = tmem + (uint32_t)(b * 256 + h * 128);
+          const uint64_t dah = dA0 + (uint64_t)((h * S::HALF_BYTES) >> 4);
+#pragma unroll
+          for (int ks = 0; ks < KP / 16; ++ks) {
+            const uint64_t ko = (uint64_t)ks * 16u;  // two 16-byte core matrices per K step
+            mma_f16(d, dah + ko, dbh + ko, IDESC, ks > 0 ? 1u : 0u);
+            mma_f16(d, dah + ko, dbh + B_LO + ko, IDESC, 1u);
+            mma_f16(d, dah + A_LO + ko, dbh + ko, IDESC, 1u);
+          }
+          mma_commit(&acc_full[2 * b + h]);
+        }
+        if (!ok) {
+          fail();
+          break;
+        }
+        mma_commit(&coef_empty[s]);
+      }
+    }
   } else {
     // ---- epilogue (tcgen05.ld 16x256b: thread t holds lanes t/4 and t/4 + 8
-    // of a 16-lane group at columns 2 (t % 4) + {0, 1} of every 8-column group,
-    // so each weight load serves eight query rows)
-    const int quad = warp & 3, grp = (warp - 4) >> 2;
+    // of a 16-lane half at columns 2 (t % 4) + {0, 1} of every 8-column group,
+    // so each weight load serves four query rows)
+    const int quad = warp & 3, h = (warp - 4) >> 2;
     const int tq = lane & 3, tr = lane >> 2;
-    // rows ri = rb * 4 + hb * 2 + s: row block rb, 16-lane group hb, lane t/4 + 8 s;
-    // .x / .y accumulate the even / odd column of the thread's pairs
-    float2 acc[8][3];
+    // rows ri = hb * 2 + r8: 16-lane half hb, lane t/4 + 8 r8; .x / .y
+    // accumulate the even / odd column of the thread's pairs
+    float2 acc[4][3];
 #pragma unroll
-    for (int r = 0; r < 8; ++r)
+    for (int r = 0; r < 4; ++r)
 #pragma unroll
       for (int c = 0; c < 3; ++c) acc[r][c] = make_float2(0.f, 0.f);
-    for (int i = 0; i < nchunks; ++i) {
+    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(h * 128);
+    // 32-column block n of buffer b: both 16-lane halves
+    auto load = [&](int b, int n, uint32_t (&v)[2][16]) {
+#pragma unroll
+      for (int hb = 0; hb < 2; ++hb)
+        tmem_ld16x256_x4_nowait(lane_base + ((uint32_t)(hb * 16) << 16) + (uint32_t)(b * 256 + n * 32),
+                                v[hb]);
+    };
+    // accumulate block n (columns 32 n + 8 k + 2 tq + {0, 1}, k = 0..3): the
+    // 32 exponentials first, in place (independent MUFU operations whose
+    // latency overlaps), then the colour sums
+    auto use = [&](const float* wp, int n, uint32_t (&v)[2][16], auto sc_tag) {
+      constexpr bool SC = decltype(sc_tag)::value;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float2 sc = make_float2(1.f, 1.f);
+        if (SC) sc = *reinterpret_cast<const float2*>(wp + (16 * n + 4 * k) * 8 + 6);
+#pragma unroll
+        for (int hb = 0; hb < 2; ++hb)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            float sv = __uint_as_float(v[hb][4 * k + j]);
+            if (SC) sv *= (j & 1) ? sc.y : sc.x;
+            v[hb][4 * k + j] = __float_as_uint(ex2_approx(sv));
+          }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float* wk = wp + (16 * n + 4 * k) * 8;
+        const float4 w01 = *reinterpret_cast<const float4*>(wk);
+        const float2 w2 = *reinterpret_cast<const float2*>(wk + 4);
+#pragma unroll
+        for (int hb = 0; hb < 2; ++hb)
+#pragma unroll
+          for (int r8 = 0; r8 < 2; ++r8) {
+            const float2 e = make_float2(__uint_as_float(v[hb][4 * k + 2 * r8]),
+                                         __uint_as_float(v[hb][4 * k + 2 * r8 + 1]));
+            const int ri = hb * 2 + r8;
+            acc[ri][0] = __ffma2_rn(make_float2(w01.x, w01.y), e, acc[ri][0]);
+            acc[ri][1] = __ffma2_rn(make_float2(w01.z, w01.w), e, acc[ri][1]);
+            acc[ri][2] = __ffma2_rn(w2, e, acc[ri][2]);
+          }
+      }
+    };
+    // one chunk: four 32-column blocks, block n + 1 loading while block n is used
+    auto chunk = [&](int b, const float* wp, auto sc_tag) {
+      uint32_t va[2][16], vb[2][16];
+      load(b, 0, va);
+      tmem_wait_ld();
+      tmem_reg_fence16(va[0]);
+      tmem_reg_fence16(va[1]);
+      load(b, 1, vb);
+      use(wp, 0, va, sc_tag);
+      tmem_wait_ld();
+      tmem_reg_fence16(vb[0]);
+      tmem_reg_fence16(vb[1]);
+      load(b, 2, va);
+      use(wp, 1, vb, sc_tag);
+      tmem_wait_ld();
+      tmem_reg_fence16(va[0]);
+      tmem_reg_fence16(va[1]);
+      load(b, 3, vb);
+      use(wp, 2, va, sc_tag);
+      tmem_wait_ld();
+      tmem_reg_fence16(vb[0]);
+      tmem_reg_fence16(vb[1]);
+      // this warp's reads of buffer b are complete
+      fence_before_sync();
+      warp_arrive(&acc_empty[2 * b + h]);
+      use(wp, 3, vb, sc_tag);
+    };
+    const bool my_block = h < nh;
+    for (int i = 0; my_block && i < nchunks; ++i) {
       const int s = i % CS, b = i & 1;
-      bool ok = warp_wait(&acc_full[b], (i >> 1) & 1, abort_flag);
+      bool ok = warp_wait(&acc_full[2 * b + h], (i >> 1) & 1, abort_flag);
       if (ok) ok = warp_wait(&coef_full[s], (i / CS) & 1, abort_flag);
       if (!ok) {
         if (lane == 0) fail();
@@ -394,97 +469,36 @@ __global__ void __launch_bounds__(384, 1) fwd_h_kernel(FwdArgs a) {
       fence_after_sync();
       const int4 fl = *reinterpret_cast<const int4*>(&sflag[s][0]);
       const bool scaled = (fl.x | fl.y | fl.z | fl.w) != 0;
-      // weight pair entries of this thread: p = 32 grp + cb / 2 + 4 k + tq
-      const float* wp = reinterpret_cast<const float*>(Cst + s * S::C_STAGE + 2 * S::B_BYTES) +
-                        (grp * 32 + tq) * 8;
-      // one 32-column block of this warp's 64 (all four lane / row groups)
-      auto block = [&](int cb, auto sc_tag) {
-        constexpr bool SC = decltype(sc_tag)::value;
-        uint32_t v[4][16];
-#pragma unroll
-        for (int rb = 0; rb < 2; ++rb)
-#pragma unroll
-          for (int hb = 0; hb < 2; ++hb)
-            tmem_ld16x256_x4_nowait(tmem + ((uint32_t)(quad * 32 + hb * 16) << 16) +
-                                        (uint32_t)(b * 256 + rb * 128 + grp * 64 + cb),
-                                    v[rb * 2 + hb]);
-        tmem_wait_ld();
-#pragma unroll
-        for (int q = 0; q < 4; ++q) tmem_reg_fence16(v[q]);
-        if (cb == 32) {  // this warp's reads of buffer b are complete
-          fence_before_sync();
-          warp_arrive(&acc_empty[b]);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float* wk = wp + ((cb >> 1) + 4 * k) * 8;
-          const float4 w01 = *reinterpret_cast<const float4*>(wk);
-          const float2 w2 = *reinterpret_cast<const float2*>(wk + 4);
-          float2 sc = make_float2(1.f, 1.f);
-          if (SC) sc = *reinterpret_cast<const float2*>(wk + 6);
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              float2 sv = make_float2(__uint_as_float(v[q][4 * k + 2 * h]),
-                                      __uint_as_float(v[q][4 * k + 2 * h + 1]));
-              if (SC) sv = __fmul2_rn(sv, sc);
-              const float2 e = make_float2(ex2_approx(sv.x), ex2_approx(sv.y));
-              const int ri = q * 2 + h;
-              acc[ri][0] = __ffma2_rn(make_float2(w01.x, w01.y), e, acc[ri][0]);
-              acc[ri][1] = __ffma2_rn(make_float2(w01.z, w01.w), e, acc[ri][1]);
-              acc[ri][2] = __ffma2_rn(w2, e, acc[ri][2]);
-            }
-        }
-      };
-#pragma unroll 1
-      for (int cb = 0; cb < 64; cb += 32) {
-        if (scaled) block(cb, BoolTag<true>{});
-        else block(cb, BoolTag<false>{});
-      }
+      // weight pair entries of this thread: p = 16 n + 4 k + tq
+      const float* wp = reinterpret_cast<const float*>(Cst + s * S::C_STAGE + 2 * S::B_BYTES) + tq * 8;
+      if (scaled) chunk(b, wp, BoolTag<true>{});
+      else chunk(b, wp, BoolTag<false>{});
       warp_arrive(&coef_empty[s]);
     }
-    // ---- row sums: over the pair halves, the four threads sharing a lane
-    // (shuffles) and the two column groups (shared memory); write y
-    float rs[8][3];
+    // ---- row sums over the pair halves and the four threads sharing a lane
+    // (shuffles); thread tq writes row ri = tq
+    if (my_block && !*abort_flag) {
 #pragma unroll
-    for (int r = 0; r < 8; ++r)
+      for (int ri = 0; ri < 4; ++ri) {
+        float rs[3];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        float v = acc[r][c].x + acc[r][c].y;
-        v += __shfl_xor_sync(0xffffffffu, v, 1);
-        v += __shfl_xor_sync(0xffffffffu, v, 2);
-        rs[r][c] = v;
-      }
-    // thread tq owns rows ri = 2 tq, 2 tq + 1
-    auto row_of = [&](int ri) {
-      return (ri >> 2) * 128 + quad * 32 + ((ri >> 1) & 1) * 16 + (ri & 1) * 8 + tr;
-    };
+        for (int c = 0; c < 3; ++c) {
+          float v = acc[ri][c].x + acc[ri][c].y;
+          v += __shfl_xor_sync(0xffffffffu, v, 1);
+          v += __shfl_xor_sync(0xffffffffu, v, 2);
+          rs[c] = v;
+        }
+        const int qr = h * 128 + quad * 32 + (ri >> 1) * 16 + (ri & 1) * 8 + tr;
+        if (ri == tq && qr < nq) {
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      if ((r >> 1) != tq) continue;
-      if (grp == 1) {
-        const int qr = row_of(r);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) red[qr * 4 + c] = rs[r][c];
-      }
-    }
-    bar_sync(2, 256);
-    if (grp == 0 && !*abort_flag) {
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        if ((r >> 1) != tq) continue;
-        const int qr = row_of(r);
-        if (qr < nq) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) a.y[(qt + qr) * 3 + c] = rs[r][c] + red[qr * 4 + c];
+          for (int c = 0; c < 3; ++c) a.y[(qt + qr) * 3 + c] = rs[c];
         }
       }
     }
   }
   fence_before_sync();
   __syncthreads();
-  if (warp == 3 && lane == 0) {
+  if (warp == 12 && lane == 0) {
     // every MMA this thread issued has completed once this commit arrives
     mma_commit(&drain);
     if (!mbar_wait_bounded(&drain, 0, kWaitLimit)) fail();
@@ -505,7 +519,7 @@ int launch_fwd_tc(int N, const FwdArgs& a, long long T, cudaStream_t s) {
   {                                                                                     \
     cudaFuncSetAttribute(fwd_h_kernel<n>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                          (int)FwdHShape<n>::SMEM);                                      \
-    fwd_h_kernel<n><<<(unsigned)T, 384, FwdHShape<n>::SMEM, s>>>(a);                    \
+    fwd_h_kernel<n><<<(unsigned)T, 416, FwdHShape<n>::SMEM, s>>>(a);                    \
   }
   switch (N) {
     NDG_H_CASE(1, L_H) NDG_H_CASE(2, L_H) NDG_H_CASE(3, L_H) NDG_H_CASE(4, L_H)
