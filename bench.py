@@ -47,11 +47,13 @@ def workload_name(g, q):
             f"cutoff 1/255, {BUCKETS} buckets, Adam lr 1e-3")
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one bwd_h_kernel<6> launch
-# (18.75 MB + 303.83 MB on the 1/8 workload, E = 2,760,083 entries), scaled to
-# a full launch by the entries processed (E = 1.0894e8, x 39.47); taken from
-# profiles/bwd_h_kernel_fit_n6.md and to be re-taken whenever the kernel changes.
-BWD_TRAFFIC = 12.73e9
+# DRAM bytes per candidate entry of one bwd_h_kernel<6> launch:
+# dram__bytes_read.sum + dram__bytes_write.sum = 19.91 MB + 298.04 MB from one
+# ncu capture of the 1/8 workload (E = 2,760,083 entries), i.e. 115.2 B per
+# entry; a full launch's traffic is this times its entries (the kernel streams
+# one gradient record per entry, so traffic grows in proportion).  To be
+# re-taken whenever the kernel changes.
+BWD_BYTES_PER_ENTRY = (19.909376e6 + 298.038784e6) / 2760083
 
 
 def flops_per_pair(N: int):
@@ -447,7 +449,8 @@ def main():
         executed = mean_pairs * exe_bwd / t_bwd / 1e12
         roofline = {"bound": "tensor", "kernel": f"bwd_h_kernel<{N_DIM}> (tcgen05 kind::f16)",
                     "achieved": round(achieved, 3), "peak": round(tc_peak, 1), "unit": "TFLOP/s",
-                    "frac": round(achieved / tc_peak, 4), "traffic": BWD_TRAFFIC,
+                    "frac": round(achieved / tc_peak, 4),
+                    "traffic": round(BWD_BYTES_PER_ENTRY * chosen["candidates_per_step"]),
                     "peak_source": f"bf16 dense sustained, {peak_kind} (FP16 operands run at "
                                    "the bf16 rate)",
                     "algorithmic": f"{alg_bwd} flop/pair (4F: recompute s, gradient contraction)",
