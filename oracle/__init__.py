@@ -177,8 +177,13 @@ def cull_exact(L, m, w, x, tile, proj, cutoff, k_sigma):
     return keep
 
 
-def cull_contract(L, m, w, x, tile, proj, cutoff, k_sigma, buckets):
-    """(offsets [T+1] int64, ids [E] int32) from the FP32 bucket contract."""
+def cull_contract(L, m, w, x, tile, proj, cutoff, k_sigma, buckets, tiles=None):
+    """(offsets, ids [E] int32) from the FP32 bucket contract.
+
+    tiles=None: every tile, offsets [T+1] int64.  Otherwise the lists of the
+    given tile indices only (in that order), offsets [len(tiles)+1]; each list
+    equals that tile's list in the full run (the ranges and keys still come
+    from the whole query set)."""
     lib = _load()
     L, pL = _d(L)
     m, pm = _d(m)
@@ -189,9 +194,16 @@ def cull_contract(L, m, w, x, tile, proj, cutoff, k_sigma, buckets):
     k = proj.shape[0]
     Q = x.shape[0]
     T = (Q + tile - 1) // tile
-    offsets = np.zeros(T + 1, dtype=np.int64)
+    if tiles is None:
+        n_sel, psel, nt = 0, None, T
+    else:
+        sel = np.ascontiguousarray(tiles, dtype=np.int64)
+        assert sel.size == 0 or (sel.min() >= 0 and sel.max() < T)
+        n_sel, psel, nt = sel.size, sel.ctypes.data_as(_LL), sel.size
+    offsets = np.zeros(nt + 1, dtype=np.int64)
     args = (N, Ge, pL, pm, pw, ctypes.c_longlong(Q), px, tile, k, pp,
-            ctypes.c_double(cutoff), ctypes.c_double(k_sigma), buckets)
+            ctypes.c_double(cutoff), ctypes.c_double(k_sigma), buckets,
+            ctypes.c_longlong(n_sel), psel)
     E = lib.oracle_cull_contract(*args, offsets.ctypes.data_as(_LL), None)
     ids = np.zeros(max(E, 1), dtype=np.int32)
     E2 = lib.oracle_cull_contract(*args, offsets.ctypes.data_as(_LL), ids.ctypes.data_as(_I))

@@ -225,11 +225,16 @@ static int bucket_raw(float v, float lo, float inv_h, int B) {
 }
 
 /* Runs the contract; writes the candidate lists as CSR (ascending ids per
- * tile).  ids may be NULL to count only.  Returns E, the total entries. */
+ * tile).  ids may be NULL to count only.  Returns E, the total entries.
+ * sel == NULL: every tile, offsets [T+1].  Otherwise only the n_sel tiles
+ * listed in sel (in that order), offsets [n_sel+1]; the global per-projection
+ * ranges and the keys are the same as for the whole query set, so each
+ * selected tile's list equals its list in the full run. */
 long long oracle_cull_contract(int N, int Ge, const double* L, const double* m,
                                const double* w, long long Q, const double* x,
                                int tile, int k, const double* proj,
                                double cutoff, double k_sigma, int B,
+                               long long n_sel, const long long* sel,
                                long long* offsets, int* ids) {
   long long T = (Q + tile - 1) / tile;
   float* xf = (float*)malloc(sizeof(float) * (size_t)(Q * N + 1));
@@ -299,22 +304,43 @@ long long oracle_cull_contract(int N, int Ge, const double* L, const double* m,
       key[2 + 2 * j] = th < 0 ? 0 : (th > B - 1 ? B - 1 : th);
     }
   }
-  long long E = 0;
-  for (long long t = 0; t < T; ++t) {
-    if (offsets) offsets[t] = E;
-    const int* tkey = tk + t * (2 * k + 1);
-    for (int g = 0; g < Ge; ++g) {
-      const int* key = gk + (size_t)g * (2 * k + 1);
-      int ok = key[0];
-      for (int j = 0; ok && j < k; ++j)
-        if (key[1 + 2 * j] > tkey[2 + 2 * j] || tkey[1 + 2 * j] > key[2 + 2 * j]) ok = 0;
-      if (ok) {
-        if (ids) ids[E] = g;
-        ++E;
+  /* Overlap test of every Gaussian against each (selected) tile: a count
+   * pass, the list offsets, then a fill pass (tiles are independent). */
+  const long long nt = sel ? n_sel : T;
+  long long* cnt = (long long*)malloc(sizeof(long long) * (size_t)(nt + 1));
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1 && !ids) break;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long long i = 0; i < nt; ++i) {
+      const long long t = sel ? sel[i] : i;
+      const int* tkey = tk + t * (2 * k + 1);
+      long long e = pass ? cnt[i] : 0;
+      for (int g = 0; g < Ge; ++g) {
+        const int* key = gk + (size_t)g * (2 * k + 1);
+        int ok = key[0];
+        for (int j = 0; ok && j < k; ++j)
+          if (key[1 + 2 * j] > tkey[2 + 2 * j] || tkey[1 + 2 * j] > key[2 + 2 * j]) ok = 0;
+        if (ok) {
+          if (pass) ids[e] = g;
+          ++e;
+        }
       }
+      if (!pass) cnt[i] = e;
+    }
+    if (pass == 0) {  /* counts -> offsets */
+      long long E = 0;
+      for (long long i = 0; i < nt; ++i) {
+        const long long c = cnt[i];
+        cnt[i] = E;
+        E += c;
+      }
+      cnt[nt] = E;
     }
   }
-  if (offsets) offsets[T] = E;
+  const long long E = cnt[nt];
+  if (offsets)
+    for (long long i = 0; i <= nt; ++i) offsets[i] = cnt[i];
+  free(cnt);
   free(xf); free(rf); free(qv); free(lo); free(hi); free(ih); free(gk); free(tk);
   return E;
 }

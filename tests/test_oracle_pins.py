@@ -259,6 +259,25 @@ def test_cull_sound_against_brute_force(oracle, cutoff, k_sigma):
             assert np.all(s[keep[:, g] == 0] > k_sigma ** 2)
 
 
+def test_cull_contract_tile_selection_matches_full_run(oracle):
+    """The contract restricted to a set of tiles (any order, repeats allowed)
+    returns exactly those tiles' lists of the full run: the per-projection
+    ranges and the keys come from the whole query set either way."""
+    tile = 64
+    mix, x, proj = _cull_case(seed=3, Q=1000)  # ragged last tile
+    raw = raw_from(oracle, mix)
+    L, m, w = oracle.activate(raw)
+    offs, ids = oracle.cull_contract(L, m, w, x, tile, proj, 1.0 / 255.0, 3.0, 64)
+    T = offs.size - 1
+    sel = np.array([T - 1, 0, 5, 5, 11], dtype=np.int64)
+    so, si = oracle.cull_contract(L, m, w, x, tile, proj, 1.0 / 255.0, 3.0, 64, tiles=sel)
+    assert so.size == sel.size + 1 and so[0] == 0
+    for i, t in enumerate(sel):
+        np.testing.assert_array_equal(si[so[i]:so[i + 1]], ids[offs[t]:offs[t + 1]])
+    eo, ei = oracle.cull_contract(L, m, w, x, tile, proj, 1.0 / 255.0, 3.0, 64, tiles=[])
+    assert eo.tolist() == [0] and ei.size == 0
+
+
 def _raw_single_rows(N, means, thetas, alphas, gammas):
     return {"mean": np.asarray(means, np.float64).reshape(-1, N),
             "theta": np.asarray(thetas, np.float64).reshape(len(alphas), -1),
