@@ -214,3 +214,49 @@ def config1(seed: int = 1, G: int = 100_000, Q: int = 1 << 20, k: int = 16) -> d
         "proj": projections(N, k, seed + 2), "target": targets_uniform(Q, seed + 3),
         "tile": 256, "cutoff": 1.0 / 255.0, "k_sigma": 3.0, "buckets": 64,
     }
+
+
+def config2(seed: int = 2, G: int = 500_000, n_planes: int = 256, res: int = 128,
+            k: int = 16) -> dict:
+    """N=10 surface queries: 500k Gaussians, 256 random planes with a 128 x 128
+    grid each (2^22 queries, 16 x 16 tiles), 16 projections, cutoff 1/255."""
+    N = 10
+    return {
+        "N": N, "mix": mixture(N, G, seed), "x": queries_planes(N, n_planes, res, seed + 1),
+        "proj": projections(N, k, seed + 2), "tile": 256, "cutoff": 1.0 / 255.0,
+        "k_sigma": 3.0, "buckets": 64,
+    }
+
+
+def config3(seed: int = 3, G: int = 50_000, G_gt: int = 2_000_000, G_max: int = 1_000_000,
+            n_planes: int = 16, res: int = 128, k: int = 16) -> dict:
+    """N=10 fit: a ground-truth mixture of 2M Gaussians drawn as in config 2,
+    a fitted mixture of 50k parents whose children start at brightness t/10
+    (t = 0.01) and may grow it to 1M, minibatches of 2^18 surface queries
+    (16 planes x 128^2), 16 projections, cutoff 1/255."""
+    N = 10
+    return {
+        "N": N, "mix": mixture(N, G, seed), "gt": mixture(N, G_gt, seed + 100),
+        "children": children(N, G, seed + 1, spread=0.05, brightness=(0.0009, 0.0011)),
+        "x": queries_planes(N, n_planes, res, seed + 2), "proj": projections(N, k, seed + 3),
+        "G_max": G_max, "t": 0.01, "tile": 256, "cutoff": 1.0 / 255.0, "k_sigma": 3.0,
+        "buckets": 64,
+    }
+
+
+def config4_frames(seed: int = 4, n: int = 64) -> list:
+    """Batched render specs: n independent frames, G log-uniform in
+    [1e4, 5e5], N in {6, 8, 10}, resolution log-uniform between 256 x 256 and
+    1920 x 1080 (one exponent for both sides), one query per pixel.  Each
+    spec carries the seeds of its mixture, queries and projections."""
+    r = rng(seed)
+    out = []
+    for i in range(n):
+        t = r.uniform()
+        out.append({
+            "N": int(r.choice([6, 8, 10])),
+            "G": int(round(np.exp(r.uniform(np.log(1e4), np.log(5e5))))),
+            "W": int(round(256 * (1920 / 256) ** t)), "H": int(round(256 * (1080 / 256) ** t)),
+            "seed": seed * 1000 + 3 * i,
+        })
+    return out
