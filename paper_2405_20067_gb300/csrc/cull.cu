@@ -386,12 +386,16 @@ __global__ void __launch_bounds__(256) cull_tile_kernel(CullTileArgs a) {
         if (KP > 0) {
           while (r + 1 < nr && rpre[r + 1] <= i) ++r;
           const long long pos = rbeg[r] + (i - rpre[r]);
-          // keys in bin-sorted order: a warp reads consecutive rows
-          const uint32_t* gk = reinterpret_cast<const uint32_t*>(a.gkey + (size_t)pos * 2 * KP);
-          uint32_t glo[W > 0 ? W : 1], ghi[W > 0 ? W : 1];
+          // keys in bin-sorted order: a warp reads consecutive rows, 16 bytes
+          // per load (rows are 2 KP = 16, 32, 48 or 64 bytes, 16-byte aligned)
+          const uint4* gk = reinterpret_cast<const uint4*>(a.gkey + (size_t)pos * 2 * KP);
+          uint32_t row[2 * W > 4 ? 2 * W : 4];
 #pragma unroll
-          for (int w = 0; w < W; ++w) { glo[w] = gk[w]; ghi[w] = gk[W + w]; }
-          pass = keys_overlap(glo, ghi, tlo, thi, W);
+          for (int v = 0; v < (2 * W) / 4; ++v) {
+            const uint4 q = __ldg(gk + v);
+            row[4 * v] = q.x; row[4 * v + 1] = q.y; row[4 * v + 2] = q.z; row[4 * v + 3] = q.w;
+          }
+          pass = keys_overlap(row, row + W, tlo, thi, W);
         } else {
           pass = true;
         }

@@ -359,7 +359,21 @@ __global__ void __launch_bounds__(256) segsum_kernel(const float* __restrict__ p
   if (e < Ge && grp < G && col < RP4) {
     const long long b = goff[e], en = goff[e + 1];
     const float4* src = reinterpret_cast<const float4*>(part);
-    for (long long j = b + grp; j < en; j += G) {
+    // four records of the group in flight at a time, added in entry order
+    long long j = b + grp;
+    for (; j + 3 * G < en; j += 4 * G) {
+      long long r[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) r[u] = perm ? (long long)__ldg(perm + j + u * G) : j + u * G;
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = __ldg(src + r[u] * RP4 + col);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        acc.x += v[u].x; acc.y += v[u].y; acc.z += v[u].z; acc.w += v[u].w;
+      }
+    }
+    for (; j < en; j += G) {
       const long long r = perm ? (long long)__ldg(perm + j) : j;
       const float4 v = __ldg(src + r * RP4 + col);
       acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;

@@ -308,7 +308,23 @@ __global__ void __launch_bounds__(256) tr_scatter(const long long* __restrict__ 
                                                   unsigned long long* __restrict__ te) {
   const long long t = blockIdx.x;
   const long long b = offsets[t], en = offsets[t + 1];
-  for (long long e = b + threadIdx.x; e < en; e += blockDim.x) {
+  // four entries per thread in flight (independent cursor atomics); the
+  // slot order inside a segment is not used (tr_rank ranks by tile)
+  long long e = b + threadIdx.x;
+  for (; e + 3 * (long long)blockDim.x < en; e += 4 * (long long)blockDim.x) {
+    int g[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) g[u] = ids[e + u * (long long)blockDim.x];
+    unsigned long long slot[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      slot[u] = (unsigned)g[u] < (unsigned)nid ? atomicAdd(cur + g[u], 1ull) : ~0ull;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (slot[u] != ~0ull)
+        te[slot[u]] = ((unsigned long long)t << 32) | (unsigned long long)(e + u * (long long)blockDim.x);
+  }
+  for (; e < en; e += blockDim.x) {
     const int g = ids[e];
     if ((unsigned)g < (unsigned)nid)
       te[atomicAdd(cur + g, 1ull)] = ((unsigned long long)t << 32) | (unsigned long long)e;
