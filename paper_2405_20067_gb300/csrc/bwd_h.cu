@@ -27,14 +27,15 @@
 // 416 threads, one CTA per SM (all 512 TMEM columns):
 //   warps 0-3   builders: coefficient rows of a chunk of 128 candidates into
 //               one of CS stages (as in the forward), one arrival per warp;
+//               after building chunk i they run the chain of chunk i - 2
+//               (thread j = candidate j = TMEM lane j of the D2 buffer), so
+//               that the epilogue only forms E;
 //   warp 12     MMA issuer (lane 0): MMA 1 of unit u + 1, then MMA 2 of unit u
 //               (TMEM: S / E buffers u & 1 at columns 128 (u & 1); D2 buffers
 //               i & 1 at 256 + NPSI (i & 1), accumulated over the chunk's units);
 //   warps 4-11  epilogue: warp w owns lanes 32 (w % 4) .. + 31 and columns
 //               64 ((w - 4) / 4) .. + 63 of each unit: e = 2^s written back in
-//               place as FP16 hi / lo (32 S columns -> 16 hi + 16 lo columns);
-//               after each chunk both groups run the chain of the previous
-//               chunk, each writing its half of the entries' records.
+//               place as FP16 hi / lo (32 S columns -> 16 hi + 16 lo columns).
 // Every wait is bounded; a timeout records NDG_ERR_TIMEOUT and the CTA lets
 // its issued MMAs finish (bounded) before it frees tensor memory.
 #include <cuda_fp16.h>
@@ -70,11 +71,11 @@ struct BwdHShape {
   static constexpr uint32_t C_BYTES = (uint32_t)NC * KP * 2;
   static constexpr uint32_t STASH = 48;  // per candidate: m~ (N), w (3), live flag, pad
   static constexpr uint32_t C_STAGE = 2 * C_BYTES + NC * 4 + NC * STASH;  // hi, lo, row factors, stash
-  // per epilogue warp: its part of 16 records staged for coalesced stores
+  // per builder warp: one half of 16 records staged for coalesced stores
   // (stride PQMAX + 1 float4 against bank conflicts)
   static constexpr uint32_t OUT_BYTES = 16u * (PQMAX + 1) * 16;
   static constexpr uint32_t SMEM_USED =
-      2 * PHI_BYTES + 2 * PSI_BYTES + CS * C_STAGE + 8 * OUT_BYTES + 128;
+      2 * PHI_BYTES + 2 * PSI_BYTES + CS * C_STAGE + 4 * OUT_BYTES + 128;
   static constexpr uint32_t SMEM = SMEM_USED > 116u * 1024u ? SMEM_USED : 116u * 1024u;
   static constexpr uint32_t TM_D2 = 256;
   static_assert(256 + 2 * NPSI <= 512, "tensor memory");
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
   uint8_t* PsiH = PhiL + S::PHI_BYTES;
   uint8_t* PsiL = PsiH + S::PSI_BYTES;
   uint8_t* Cst = PsiL + S::PSI_BYTES;  // CS stages of (hi, lo, row factors)
-  float4* Outs = reinterpret_cast<float4*>(Cst + CS * S::C_STAGE);  // 8 x OUT_BYTES
+  float4* Outs = reinterpret_cast<float4*>(Cst + CS * S::C_STAGE);  // 4 x OUT_BYTES
   __shared__ uint64_t coef_full[CS], coef_empty[CS], s_full[2], e_full[2], d2_full[2], d2_empty[2],
       drain;
   __shared__ uint32_t tmem_base;
@@ -167,13 +168,13 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
   if (tid == 0) {
     for (int i = 0; i < CS; ++i) {
       mbar_init(&coef_full[i], 4);
-      mbar_init(&coef_empty[i], 1 + 8 + 8);  // MMA 1, epilogue warps, chain warps
+      mbar_init(&coef_empty[i], 1 + 8 + 4);  // MMA 1, epilogue warps, builders' chain
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&s_full[i], 1);
       mbar_init(&e_full[i], 8);
       mbar_init(&d2_full[i], 1);
-      mbar_init(&d2_empty[i], 8);
+      mbar_init(&d2_empty[i], 4);
     }
     mbar_init(&drain, 1);
     s_abort = 0;
@@ -363,6 +364,124 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
       warp_arrive(&coef_full[s]);
       return true;
     };
+    // Chain of entry (candidate j, chunk ic).  From D2 = sum_q e dy' phi' the
+    // gradient with respect to the unscaled lifted coefficients is
+    // Gc_k = -1/2 h_k dys sum_c w_c D2[c][k] and dl/dw_c = dys D2[c][P + N]
+    // (the constant feature); the record is the frame-free [G = dl/dA
+    // (symmetric, lower packed), v = Gc0 m~ - G_lin, dl/dw] (dl/dM = 2 M sum G
+    // and dl/dm = 2 A sum v follow per Gaussian).  The record is formed in two
+    // halves of positions (fewer live registers), each loading only the D2
+    // columns it needs.
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    auto half = [&](int ic, const float (&sv)[12], auto gtag) {
+      constexpr int GG = decltype(gtag)::value;
+      constexpr int RPT = S::RPT, SPLIT = S::SPLIT;
+      constexpr int p0 = GG ? SPLIT : 0, p1 = GG ? RPT : SPLIT, PW = p1 - p0, PQ = PW / 4;
+      const int db = ic & 1;
+      const bool live = __float_as_int(sv[N + 3]) >= 0;
+      constexpr uint32_t KM = chain_kmask<N>(p0, p1);  // needed Gc_k (F <= 28 bits)
+      float Gc[F], gw[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < F; ++k) Gc[k] = 0.0f;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        uint32_t v[KP];
+#pragma unroll
+        for (int b = 0; b < KP / 8; ++b)
+          if ((KM >> (8 * b)) & 0xffu)
+            tmem_ld8_nowait(tmem + lane_off + S::TM_D2 + (uint32_t)(db * NPSI + c * KP + 8 * b), v + 8 * b);
+        tmem_wait_ld();
+#pragma unroll
+        for (int b = 0; b < KP / 8; ++b)
+          if ((KM >> (8 * b)) & 0xffu) tmem_reg_fence8(v + 8 * b);
+        const float wc = sv[N + c];
+#pragma unroll
+        for (int k = 0; k < F; ++k)
+          if ((KM >> k) & 1u) Gc[k] = fmaf(wc, __uint_as_float(v[k]), Gc[k]);
+        gw[c] = __uint_as_float(v[P + N]);
+      }
+      const float gsc = -0.5f * s_dys;
+#pragma unroll
+      for (int d = 0; d < N; ++d)
+#pragma unroll
+        for (int e = 0; e <= d; ++e)
+          if ((KM >> (tri(d) + e)) & 1u) Gc[tri(d) + e] *= gsc * (hsc[d] * hsc[e]);
+#pragma unroll
+      for (int d = 0; d < N; ++d)
+        if ((KM >> (P + d)) & 1u) Gc[P + d] *= gsc * hsc[d];
+      Gc[P + N] *= gsc;
+      const float Gc0 = Gc[P + N];
+      float val[PW];
+#pragma unroll
+      for (int k = 0; k < PW; ++k) val[k] = 0.0f;
+#pragma unroll
+      for (int d = 0; d < N; ++d)
+#pragma unroll
+        for (int e = 0; e <= d; ++e) {
+          const int p = tri(d) + e;
+          if (p >= p0 && p < p1) {
+            const float mi = sv[d], mk = sv[e];
+            val[p - p0] = (d == e) ? Gc[p] - 2.0f * Gc[P + d] * mi + Gc0 * mi * mi
+                                   : Gc[p] - (Gc[P + d] * mk + Gc[P + e] * mi) + Gc0 * mi * mk;
+          }
+        }
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (P + i >= p0 && P + i < p1) val[P + i - p0] = Gc0 * sv[i] - Gc[P + i];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        if (P + N + c >= p0 && P + N + c < p1) val[P + N + c - p0] = gw[c] * s_dys;
+      if (!live) {
+#pragma unroll
+        for (int k = 0; k < PW; ++k) val[k] = 0.0f;
+      }
+      // The warp's 32 records are consecutive entries: stage this half of 16
+      // records at a time and store with coalesced accesses; entries past the
+      // tile's end are not written.
+      const long long w0 = beg + (long long)ic * NC + warp * 32;
+      const long long nval = end - w0 < 32 ? end - w0 : 32;
+      float4* stg = Outs + warp * (16 * (S::PQMAX + 1));
+      float4* dst = reinterpret_cast<float4*>(a.part) + w0 * S::RQT + p0 / 4;
+#pragma unroll
+      for (int hb = 0; hb < 2; ++hb) {
+        if ((lane >> 4) == hb) {
+          const int r = lane & 15;
+#pragma unroll
+          for (int k = 0; k < PQ; ++k)
+            stg[r * (S::PQMAX + 1) + k] =
+                make_float4(val[4 * k], val[4 * k + 1], val[4 * k + 2], val[4 * k + 3]);
+        }
+        __syncwarp();
+        const int nrec = (int)(nval - 16 * hb < 0 ? 0 : (nval - 16 * hb < 16 ? nval - 16 * hb : 16));
+#pragma unroll
+        for (int m = 0; m < (16 * PQ + 31) / 32; ++m) {
+          const int idx = m * 32 + lane;
+          const int r = idx / PQ, k = idx - r * PQ;
+          if (r < nrec) dst[(long long)(16 * hb + r) * S::RQT + k] = stg[r * (S::PQMAX + 1) + k];
+        }
+        __syncwarp();
+      }
+    };
+    auto chain = [&](int ic) -> bool {
+      const int db = ic & 1, s = ic % CS;
+      float sv[12];
+      {
+        const float4* stp = reinterpret_cast<const float4*>(Cst + s * S::C_STAGE + 2 * S::C_BYTES +
+                                                            NC * 4 + (uint32_t)j * S::STASH);
+        const float4 v0 = stp[0], v1 = stp[1], v2 = stp[2];
+        sv[0] = v0.x; sv[1] = v0.y; sv[2] = v0.z; sv[3] = v0.w;
+        sv[4] = v1.x; sv[5] = v1.y; sv[6] = v1.z; sv[7] = v1.w;
+        sv[8] = v2.x; sv[9] = v2.y; sv[10] = v2.z; sv[11] = v2.w;
+      }
+      warp_arrive(&coef_empty[s]);
+      if (!warp_wait(&d2_full[db], (ic >> 1) & 1, abort_flag)) return false;
+      fence_after_sync();
+      half(ic, sv, IntTag<0>{});
+      half(ic, sv, IntTag<1>{});
+      fence_before_sync();
+      warp_arrive(&d2_empty[db]);
+      return true;
+    };
     float4 cur[R4], nxt[R4];
     const int2 c0i = cand(0);
     load(c0i.x, cur);
@@ -377,11 +496,14 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
       slot_cur = slot_nxt;
 #pragma unroll
       for (int k = 0; k < R4; ++k) cur[k] = nxt[k];
+      // the chain of chunk i - 2 (its D2 buffer is the one chunk i will use)
+      if (ok && i >= 2) ok = chain(i - 2);
       if (__shfl_sync(0xffffffffu, (!ok || *abort_flag) ? 1 : 0, 0)) {
         ok = false;
         break;
       }
     }
+    for (int ic = nchunks >= 2 ? nchunks - 2 : 0; ok && ic < nchunks; ++ic) ok = chain(ic);
     if (!ok && lane == 0) fail();
   } else if (warp == 12) {
     // ---- MMA issuer
@@ -447,120 +569,6 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
     float hsc[N];
 #pragma unroll
     for (int d = 0; d < N; ++d) hsc[d] = sh[d];
-    // Chain of entry (candidate j, chunk ic), split between the two groups by
-    // record position.  From D2 = sum_q e dy' phi' the gradient with respect
-    // to the unscaled lifted coefficients is Gc_k = -1/2 h_k dys sum_c w_c
-    // D2[c][k] and dl/dw_c = dys D2[c][P + N] (the constant feature); the
-    // record is the frame-free [G = dl/dA (symmetric, lower packed), v = Gc0 m~
-    // - G_lin, dl/dw] (dl/dM = 2 M sum G and dl/dm = 2 A sum v follow per
-    // Gaussian).  Group g writes positions [g SPLIT, ...).
-    auto chain = [&](int ic, auto gtag) -> bool {
-      constexpr int GG = decltype(gtag)::value;
-      constexpr int RPT = S::RPT, SPLIT = S::SPLIT;
-      constexpr int p0 = GG ? SPLIT : 0, p1 = GG ? RPT : SPLIT, PW = p1 - p0, PQ = PW / 4;
-      const int db = ic & 1, s = ic % CS;
-      float sv[12];
-      {
-        const float4* stp = reinterpret_cast<const float4*>(Cst + s * S::C_STAGE + 2 * S::C_BYTES +
-                                                            NC * 4 + (uint32_t)j * S::STASH);
-        const float4 v0 = stp[0], v1 = stp[1], v2 = stp[2];
-        sv[0] = v0.x; sv[1] = v0.y; sv[2] = v0.z; sv[3] = v0.w;
-        sv[4] = v1.x; sv[5] = v1.y; sv[6] = v1.z; sv[7] = v1.w;
-        sv[8] = v2.x; sv[9] = v2.y; sv[10] = v2.z; sv[11] = v2.w;
-      }
-      warp_arrive(&coef_empty[s]);
-      const bool live = __float_as_int(sv[N + 3]) >= 0;
-      if (!warp_wait(&d2_full[db], (ic >> 1) & 1, abort_flag)) return false;
-      fence_after_sync();
-      constexpr uint32_t KM = chain_kmask<N>(p0, p1);  // needed Gc_k (F <= 28 bits)
-      float Gc[F], gw[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-      for (int k = 0; k < F; ++k) Gc[k] = 0.0f;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        uint32_t v[KP];
-#pragma unroll
-        for (int b = 0; b < KP / 8; ++b)
-          if ((KM >> (8 * b)) & 0xffu)
-            tmem_ld8_nowait(tmem + lane_off + S::TM_D2 + (uint32_t)(db * NPSI + c * KP + 8 * b), v + 8 * b);
-        tmem_wait_ld();
-#pragma unroll
-        for (int b = 0; b < KP / 8; ++b)
-          if ((KM >> (8 * b)) & 0xffu) tmem_reg_fence8(v + 8 * b);
-        const float wc = sv[N + c];
-#pragma unroll
-        for (int k = 0; k < F; ++k)
-          if ((KM >> k) & 1u) Gc[k] = fmaf(wc, __uint_as_float(v[k]), Gc[k]);
-        gw[c] = __uint_as_float(v[P + N]);
-      }
-      fence_before_sync();
-      warp_arrive(&d2_empty[db]);
-      const float gsc = -0.5f * s_dys;
-#pragma unroll
-      for (int d = 0; d < N; ++d)
-#pragma unroll
-        for (int e = 0; e <= d; ++e)
-          if ((KM >> (tri(d) + e)) & 1u) Gc[tri(d) + e] *= gsc * (hsc[d] * hsc[e]);
-#pragma unroll
-      for (int d = 0; d < N; ++d)
-        if ((KM >> (P + d)) & 1u) Gc[P + d] *= gsc * hsc[d];
-      Gc[P + N] *= gsc;
-      const float Gc0 = Gc[P + N];
-      float val[PW];
-#pragma unroll
-      for (int k = 0; k < PW; ++k) val[k] = 0.0f;
-#pragma unroll
-      for (int d = 0; d < N; ++d)
-#pragma unroll
-        for (int e = 0; e <= d; ++e) {
-          const int p = tri(d) + e;
-          if (p >= p0 && p < p1) {
-            const float mi = sv[d], mk = sv[e];
-            val[p - p0] = (d == e) ? Gc[p] - 2.0f * Gc[P + d] * mi + Gc0 * mi * mi
-                                   : Gc[p] - (Gc[P + d] * mk + Gc[P + e] * mi) + Gc0 * mi * mk;
-          }
-        }
-#pragma unroll
-      for (int i = 0; i < N; ++i)
-        if (P + i >= p0 && P + i < p1) val[P + i - p0] = Gc0 * sv[i] - Gc[P + i];
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        if (P + N + c >= p0 && P + N + c < p1) val[P + N + c - p0] = gw[c] * s_dys;
-      if (!live) {
-#pragma unroll
-        for (int k = 0; k < PW; ++k) val[k] = 0.0f;
-      }
-      // The warp's 32 records are consecutive entries: stage this group's
-      // part of 16 records at a time and store with coalesced accesses;
-      // entries past the tile's end are not written.
-      const long long w0 = beg + (long long)ic * NC + quad * 32;
-      const long long nval = end - w0 < 32 ? end - w0 : 32;
-      float4* stg = Outs + (warp - 4) * (16 * (S::PQMAX + 1));
-      float4* dst = reinterpret_cast<float4*>(a.part) + w0 * S::RQT + p0 / 4;
-#pragma unroll
-      for (int hb = 0; hb < 2; ++hb) {
-        if ((lane >> 4) == hb) {
-          const int r = lane & 15;
-#pragma unroll
-          for (int k = 0; k < PQ; ++k)
-            stg[r * (S::PQMAX + 1) + k] =
-                make_float4(val[4 * k], val[4 * k + 1], val[4 * k + 2], val[4 * k + 3]);
-        }
-        __syncwarp();
-        const int nrec = (int)(nval - 16 * hb < 0 ? 0 : (nval - 16 * hb < 16 ? nval - 16 * hb : 16));
-#pragma unroll
-        for (int m = 0; m < (16 * PQ + 31) / 32; ++m) {
-          const int idx = m * 32 + lane;
-          const int r = idx / PQ, k = idx - r * PQ;
-          if (r < nrec) dst[(long long)(16 * hb + r) * S::RQT + k] = stg[r * (S::PQMAX + 1) + k];
-        }
-        __syncwarp();
-      }
-      return true;
-    };
-    auto chain_g = [&](int ic) -> bool {
-      return grp == 0 ? chain(ic, IntTag<0>{}) : chain(ic, IntTag<1>{});
-    };
     float back = 1.0f;
     bool ok = true;
     for (int u = 0; u < U; ++u) {
@@ -597,17 +605,11 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
       tmem_wait_st();
       fence_before_sync();
       warp_arrive(&e_full[sb]);
-      // chain of the previous chunk (both groups, each its half of the records)
-      if (h == nh - 1 && i >= 1) {
-        ok = chain_g(i - 1);
-        if (!ok) break;
-      }
       if (__shfl_sync(0xffffffffu, *abort_flag ? 1 : 0, 0)) {
         ok = false;
         break;
       }
     }
-    if (ok && nchunks >= 1) ok = chain_g(nchunks - 1);
     if (!ok && lane == 0) fail();
   }
   fence_before_sync();
