@@ -66,7 +66,13 @@ struct BwdHShape {
   static constexpr uint32_t SBO_K = (KP / 8) * 128;   // rows of KP FP16 values
   static constexpr uint32_t SBO_Q = (256 / 8) * 128;  // Psi rows of 256 queries
   static constexpr uint32_t PHI_BYTES = 256u * KP * 2;
-  static constexpr uint32_t HALF_BYTES = 128u * KP * 2;
+  // queries per unit (MMA 1 N, MMA 2 K).  128: two S / E buffers, MMA 1 one
+  // unit ahead of MMA 2.  (64 with four buffers, MMA 1 three units ahead,
+  // measured 27% slower: an MMA's cost has a floor of ~46 cycles, so the
+  // narrower MMA 1 and the doubled per-unit overheads outweigh the slack.)
+  static constexpr int UQ = 128;
+  static constexpr int NBUF = 256 / UQ;     // S / E buffers in TMEM columns [0, 256)
+  static constexpr uint32_t UNIT_BYTES = (uint32_t)UQ * KP * 2;  // Phi rows of one unit
   static constexpr uint32_t PSI_BYTES = (uint32_t)NPSI * 256 * 2;
   static constexpr uint32_t C_BYTES = (uint32_t)NC * KP * 2;
   static constexpr uint32_t STASH = 48;  // per candidate: m~ (N), w (3), live flag, pad
@@ -152,7 +158,7 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
   uint8_t* PsiL = PsiH + S::PSI_BYTES;
   uint8_t* Cst = PsiL + S::PSI_BYTES;  // CS stages of (hi, lo, row factors)
   float4* Outs = reinterpret_cast<float4*>(Cst + CS * S::C_STAGE);  // 4 x OUT_BYTES
-  __shared__ uint64_t coef_full[CS], coef_empty[CS], s_full[2], e_full[2], d2_full[2], d2_empty[2],
+  __shared__ uint64_t coef_full[CS], coef_empty[CS], s_full[S::NBUF], e_full[S::NBUF], d2_full[2], d2_empty[2],
       drain;
   __shared__ uint32_t tmem_base;
   __shared__ float sred[8 * N * 2], sdy[8];
@@ -163,16 +169,18 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
   const long long t = blockIdx.x;
   const long long qt = t * a.tile;
   const int nq = (int)(a.Q - qt < a.tile ? a.Q - qt : a.tile);
-  const int nh = nq > 128 ? 2 : 1;  // units (128-query blocks) per chunk
+  const int nh = (nq + S::UQ - 1) / S::UQ;  // units (blocks of UQ queries) per chunk
 
   if (tid == 0) {
     for (int i = 0; i < CS; ++i) {
       mbar_init(&coef_full[i], 4);
       mbar_init(&coef_empty[i], 1 + 8 + 4);  // MMA 1, epilogue warps, builders' chain
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < S::NBUF; ++i) {
       mbar_init(&s_full[i], 1);
       mbar_init(&e_full[i], 8);
+    }
+    for (int i = 0; i < 2; ++i) {
       mbar_init(&d2_full[i], 1);
       mbar_init(&d2_empty[i], 4);
     }
@@ -508,7 +516,7 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
   } else if (warp == 12) {
     // ---- MMA issuer
     if (lane == 0 && U > 0) {
-      constexpr uint32_t IDESC1 = idesc_f16(128);
+      constexpr uint32_t IDESC1 = idesc_f16(S::UQ);
       constexpr uint32_t IDESC2 = idesc_f16(NPSI);
       // descriptor bases (a descriptor for base + off is base + off / 16)
       const uint64_t dPhi = smem_desc(smem_u32(PhiH), 128, S::SBO_K);
@@ -517,12 +525,12 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
       constexpr uint64_t PHI_LO = S::PHI_BYTES >> 4, PSI_LO = S::PSI_BYTES >> 4;
       constexpr uint64_t C_LO = S::C_BYTES >> 4;
       auto mma1 = [&](int u) -> bool {
-        const int i = u / nh, h = u - i * nh, s = i % CS, sb = u & 1;
+        const int i = u / nh, h = u - i * nh, s = i % CS, sb = u % S::NBUF;
         if (h == 0 && !mbar_wait_sleep(&coef_full[s], (i / CS) & 1, abort_flag)) return false;
         fence_after_sync();
         const uint64_t dch = dC0 + (uint64_t)((s * S::C_STAGE) >> 4);
-        const uint64_t dph = dPhi + (uint64_t)((h * S::HALF_BYTES) >> 4);
-        const uint32_t d = tmem + (uint32_t)(sb * 128);
+        const uint64_t dph = dPhi + (uint64_t)((h * S::UNIT_BYTES) >> 4);
+        const uint32_t d = tmem + (uint32_t)(sb * S::UQ);
 #pragma unroll
         for (int ks = 0; ks < KP / 16; ++ks) {
           const uint64_t ko = (uint64_t)ks * 16u;  // 256 bytes per K step
@@ -535,16 +543,16 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
         return true;
       };
       auto mma2 = [&](int u) -> bool {
-        const int i = u / nh, h = u - i * nh, sb = u & 1, db = i & 1;
-        if (!mbar_wait_sleep(&e_full[sb], (u >> 1) & 1, abort_flag)) return false;
+        const int i = u / nh, h = u - i * nh, sb = u % S::NBUF, db = i & 1;
+        if (!mbar_wait_sleep(&e_full[sb], (u / S::NBUF) & 1, abort_flag)) return false;
         if (h == 0 && i >= 2 && !mbar_wait_sleep(&d2_empty[db], ((i >> 1) - 1) & 1, abort_flag))
           return false;
         fence_after_sync();
         const uint32_t d = tmem + S::TM_D2 + (uint32_t)(db * NPSI);
-        const uint32_t e0 = tmem + (uint32_t)(sb * 128);
-        const uint64_t dsh = dPsi + (uint64_t)(16 * h) * 8u;
+        const uint32_t e0 = tmem + (uint32_t)(sb * S::UQ);
+        const uint64_t dsh = dPsi + (uint64_t)((S::UQ / 8) * h) * 8u;  // 128 B per 8 queries
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {  // 16 queries per K step
+        for (int kk = 0; kk < S::UQ / 16; ++kk) {  // 16 queries per K step
           const uint32_t eh = e0 + (uint32_t)(32 * (kk >> 1) + 8 * (kk & 1));
           const uint64_t qo = (uint64_t)(2 * kk) * 8u;
           mma_f16_ts(d, eh, dsh + qo, IDESC2, (h > 0 || kk > 0) ? 1u : 0u);
@@ -554,9 +562,14 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
         if (h == nh - 1) mma_commit(&d2_full[db]);
         return true;
       };
-      bool ok = mma1(0);
+      // MMA 1 runs NBUF - 1 units ahead of MMA 2 (MMAs execute in issue
+      // order, so MMA 1 of unit u + NBUF - 1 overwrites buffer (u - 1) % NBUF
+      // only after MMA 2 of unit u - 1 has read it)
+      constexpr int LEAD = S::NBUF - 1;
+      bool ok = true;
+      for (int u = 0; ok && u < LEAD && u < U; ++u) ok = mma1(u);
       for (int u = 0; ok && u < U; ++u) {
-        if (u + 1 < U) ok = mma1(u + 1);
+        if (u + LEAD < U) ok = mma1(u + LEAD);
         if (ok) ok = mma2(u);
       }
       if (!ok) fail();
@@ -572,8 +585,8 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
     float back = 1.0f;
     bool ok = true;
     for (int u = 0; u < U; ++u) {
-      const int i = u / nh, h = u - i * nh, s = i % CS, sb = u & 1;
-      ok = warp_wait(&s_full[sb], (u >> 1) & 1, abort_flag);
+      const int i = u / nh, h = u - i * nh, s = i % CS, sb = u % S::NBUF;
+      ok = warp_wait(&s_full[sb], (u / S::NBUF) & 1, abort_flag);
       if (ok && h == 0) ok = warp_wait(&coef_full[s], (i / CS) & 1, abort_flag);
       if (!ok) break;
       fence_after_sync();
@@ -581,16 +594,17 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
         back = reinterpret_cast<const float*>(Cst + s * S::C_STAGE + 2 * S::C_BYTES)[j];
         warp_arrive(&coef_empty[s]);
       }
-      // all 64 columns of this warp in flight at once, one wait
-      const uint32_t col = tmem + lane_off + (uint32_t)(sb * 128 + grp * 64);
-      uint32_t v[64];
+      // all UQ / 2 columns of this warp in flight at once, one wait
+      constexpr int WC = S::UQ / 2;
+      const uint32_t col = tmem + lane_off + (uint32_t)(sb * S::UQ + grp * WC);
+      uint32_t v[WC];
 #pragma unroll
-      for (int cb = 0; cb < 64; cb += 16) tmem_ld16_nowait(col + (uint32_t)cb, v + cb);
+      for (int cb = 0; cb < WC; cb += 16) tmem_ld16_nowait(col + (uint32_t)cb, v + cb);
       tmem_wait_ld();
 #pragma unroll
-      for (int cb = 0; cb < 64; cb += 16) tmem_reg_fence16(v + cb);
+      for (int cb = 0; cb < WC; cb += 16) tmem_reg_fence16(v + cb);
 #pragma unroll
-      for (int cb = 0; cb < 64; cb += 32) {
+      for (int cb = 0; cb < WC; cb += 32) {
         uint32_t hi[16], lo[16];
 #pragma unroll
         for (int p = 0; p < 16; ++p) {
