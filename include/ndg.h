@@ -147,9 +147,20 @@ ndg_status ndg_build_cull(const ndg_mixture* mix, const ndg_queries* q,
                            hi/lo operands (3 products) with exact power-of-two
                            scaling, FP32 accumulation; N <= 12; outputs within
                            ~2e-4 relative of the FP64 definition */
+#define NDG_MODE_AUTO 2 /* forward: per tile, NDG_MODE_TC where the tile has
+                           at least NDG_AUTO_MIN_CANDIDATES(N) candidates (the
+                           contraction is dense enough for 128-candidate
+                           tensor-core chunks), NDG_MODE_FP32 elsewhere; each
+                           tile's outputs equal those of the mode it gets.
+                           backward: NDG_MODE_TC for N <= 6, else FP32 */
+/* Crossover measured on GB300 with full tiles of 256 queries: the two forms
+ * take equal time at about 190 candidates per tile for N = 6 and about 110
+ * for N = 10. */
+#define NDG_AUTO_MIN_CANDIDATES(N) ((N) <= 6 ? 192 : 128)
 
 /* Eq. 1 and Eq. 8: y [Q][3] = culled mixture sum at every query.  `cull`
- * must come from ndg_build_cull on the same mixture and queries. */
+ * must come from ndg_build_cull on the same mixture and queries.  mode:
+ * NDG_MODE_FP32, NDG_MODE_TC or NDG_MODE_AUTO (else NDG_ERR_INVALID_ARG). */
 ndg_status ndg_forward(const ndg_mixture* mix, const ndg_queries* q,
                        const ndg_cull* cull, int mode, float* y, void* ws,
                        size_t ws_bytes, ndg_stream stream, ndg_trace* trace);

@@ -6,7 +6,8 @@
 // same offset (calls sharing a workspace are ordered on one stream, and the
 // call-specific parts only hold temporaries of the call that owns them):
 //   common : header (status word), loss partial sums, prepared records
-//            [2 G_cap][R], densify scratch (flag, rank, fresh: [G_cap] each)
+//            [2 G_cap][R], densify scratch (flag, rank, fresh: [G_cap] each),
+//            the forward's tile lists of NDG_MODE_AUTO ([2 T + 2])
 //   cull   : per-tile projection bounds and bucket keys, per-Gaussian bucket
 //            keys and bins, the bin sort's buffers and offsets, per-tile
 //            counts and their scan, sort / scan temporaries
@@ -44,7 +45,7 @@ struct Sizes {
 };
 
 struct CommonLayout {
-  size_t header, rec, loss, dflag, drank, dfresh, end;
+  size_t header, rec, loss, dflag, drank, dfresh, tlist, end;
 };
 struct CullLayout {
   size_t tb, range, tkey, gkey, gkey_sorted, bin, bk_a, bv_a, bk_b, bv_b, binoff, counts, excl, masks,
@@ -63,6 +64,8 @@ CommonLayout common_layout(const Sizes& z) {
   c.dflag = r.take((size_t)z.G_cap * sizeof(int));
   c.drank = r.take((size_t)z.G_cap * sizeof(int));
   c.dfresh = r.take((size_t)z.G_cap * sizeof(int));
+  // NDG_MODE_AUTO: the dense and sparse tile lists and their counts
+  c.tlist = r.take(((size_t)2 * z.T + 2) * sizeof(int));
   c.end = r.off;
   return c;
 }
@@ -336,7 +339,8 @@ ndg_status ndg_forward(const ndg_mixture* mix, const ndg_queries* q, const ndg_c
                        ndg_trace* trace) {
   ndg_status st;
   if ((st = check_mix(mix)) || (st = check_queries(q)) || (st = check_cull(cull))) return st;
-  if (mode != NDG_MODE_FP32 && mode != NDG_MODE_TC) return NDG_ERR_INVALID_ARG;
+  if (mode != NDG_MODE_FP32 && mode != NDG_MODE_TC && mode != NDG_MODE_AUTO)
+    return NDG_ERR_INVALID_ARG;
   if (q->Q > 0 && !y) return NDG_ERR_INVALID_ARG;
   if (!ws || !aligned(ws, kAlign)) return NDG_ERR_INVALID_ARG;
   Sizes z = make_sizes(mix, q, nullptr, 0);
@@ -347,7 +351,8 @@ ndg_status ndg_forward(const ndg_mixture* mix, const ndg_queries* q, const ndg_c
   char* w = (char*)ws;
   PrepArgs pa = prep_args(mix);
   pa.rec = (float*)(w + c.rec);
-  pa.rec_kind = mode == NDG_MODE_TC ? 1 : 0;
+  // AUTO: records with both A (tensor-core form) and M (FP32 form)
+  pa.rec_kind = mode == NDG_MODE_AUTO ? 2 : (mode == NDG_MODE_TC ? 1 : 0);
   pa.status = &reinterpret_cast<WsHeader*>(w + c.header)->status;
   tr += launch_prep(mix->N, pa, s);
   FwdArgs fa{};
@@ -360,6 +365,28 @@ ndg_status ndg_forward(const ndg_mixture* mix, const ndg_queries* q, const ndg_c
   fa.Ge = pa.Ge;
   fa.y = y;
   fa.status = pa.status;
+  if (mode == NDG_MODE_AUTO) {
+    // per tile: the tensor-core form where the candidate list makes the
+    // contraction dense, the FP32 form elsewhere (the same kernels as the
+    // two fixed modes, so each tile's outputs equal that mode's)
+    int* lists = (int*)(w + c.tlist);
+    int* n_dense = lists + 2 * z.T;
+    cudaMemsetAsync(n_dense, 0, 2 * sizeof(int), s);
+    tr += launch_tile_split(cull->offsets, z.T, NDG_AUTO_MIN_CANDIDATES(mix->N), lists, lists + z.T,
+                            n_dense, n_dense + 1, s);
+    FwdArgs ft = fa, ff = fa;
+    ft.rec_stride4 = ff.rec_stride4 = rec_tc_floats(mix->N) / 4;
+    ft.tiles = lists;
+    ft.n_tiles = n_dense;
+    ff.tiles = lists + z.T;
+    ff.n_tiles = n_dense + 1;
+    ff.mat_off4 = rec_floats(mix->N) / 4;
+    tr.begin();
+    tr += launch_fwd_tc(mix->N, ft, z.T, s);
+    tr += launch_fwd(mix->N, ff, z.T, s);
+    tr.end();
+    return cuda_ok();
+  }
   tr.begin();
   tr += mode == NDG_MODE_TC ? launch_fwd_tc(mix->N, fa, z.T, s) : launch_fwd(mix->N, fa, z.T, s);
   tr.end();
@@ -386,6 +413,7 @@ ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q, const ndg_
                         ndg_stream stream, ndg_trace* trace) {
   ndg_status st;
   if ((st = check_mix(mix)) || (st = check_queries(q)) || (st = check_cull(cull))) return st;
+  if (mode == NDG_MODE_AUTO) mode = mix->N <= 6 ? NDG_MODE_TC : NDG_MODE_FP32;
   if (mode != NDG_MODE_FP32 && (mode != NDG_MODE_TC || mix->N > 6)) return NDG_ERR_INVALID_ARG;
   if (!grad || grad->N != mix->N || grad->G != mix->G || grad->has_children != mix->has_children ||
       (st = check_mix(grad)))

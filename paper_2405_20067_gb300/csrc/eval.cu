@@ -40,7 +40,9 @@ __global__ void __launch_bounds__(128) fwd_kernel(FwdArgs a) {
   __shared__ __align__(16) float spair[CH / 2 * RR];
   __shared__ float sred[4 * N * 2];
   __shared__ float sctr[N];
-  const long long t = blockIdx.x;
+  // tile of this CTA (a tile list selects a subset; surplus CTAs leave at once)
+  if (a.tiles && (int)blockIdx.x >= *a.n_tiles) return;
+  const long long t = a.tiles ? (long long)a.tiles[blockIdx.x] : (long long)blockIdx.x;
   const int tid = threadIdx.x;
   const long long q0 = t * a.tile;
   const int nq = (int)(a.Q - q0 < a.tile ? a.Q - q0 : a.tile);
@@ -67,12 +69,19 @@ __global__ void __launch_bounds__(128) fwd_kernel(FwdArgs a) {
       float M[P], m[N], w[3];
       const int g = tid < n ? a.ids[c0 + tid] : -1;
       if ((unsigned)g < (unsigned)a.Ge) {
-        const float4* src = reinterpret_cast<const float4*>(a.rec) + (size_t)g * R4;
+        // record [M, m, w] (M first), or a record whose M sits at mat_off4
+        const int stride4 = a.rec_stride4 > 0 ? a.rec_stride4 : R4;
+        const float4* src = reinterpret_cast<const float4*>(a.rec) + (size_t)g * stride4;
         float buf[R];
 #pragma unroll
         for (int i = 0; i < R4; ++i) {
           float4 v = __ldg(src + i);
           buf[4 * i] = v.x; buf[4 * i + 1] = v.y; buf[4 * i + 2] = v.z; buf[4 * i + 3] = v.w;
+        }
+        if (a.mat_off4 > 0) {
+          const float* ms = reinterpret_cast<const float*>(src + a.mat_off4);
+#pragma unroll
+          for (int i = 0; i < P; ++i) buf[i] = __ldg(ms + i);
         }
 #pragma unroll
         for (int i = 0; i < P; ++i) M[i] = kKappa * buf[i];
@@ -607,6 +616,28 @@ __global__ void __launch_bounds__(128) chain_kernel(ChainArgs a) {
     NDG_CASE_N(9, call) NDG_CASE_N(10, call) NDG_CASE_N(11, call) NDG_CASE_N(12, call) \
     default: break;                                                                   \
   }
+
+// Splits the tiles by candidate count: tiles with at least min_cand
+// candidates go to list a, the others to list b (counts in n_a, n_b, zeroed
+// by the caller).  The order inside a list does not matter: every tile's
+// outputs are computed by one CTA of one kernel.
+__global__ void tile_split_kernel(const long long* __restrict__ offsets, long long T,
+                                  long long min_cand, int* __restrict__ la, int* __restrict__ lb,
+                                  int* __restrict__ n_a, int* __restrict__ n_b) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  const bool dense = offsets[t + 1] - offsets[t] >= min_cand;
+  if (dense) la[atomicAdd(n_a, 1)] = (int)t;
+  else lb[atomicAdd(n_b, 1)] = (int)t;
+}
+
+int launch_tile_split(const long long* offsets, long long T, long long min_cand, int* la, int* lb,
+                      int* n_a, int* n_b, cudaStream_t s) {
+  if (T <= 0) return 0;
+  tile_split_kernel<<<(unsigned)ceil_div<long long>(T, 256), 256, 0, s>>>(offsets, T, min_cand, la,
+                                                                         lb, n_a, n_b);
+  return 1;
+}
 
 int launch_fwd(int N, const FwdArgs& a, long long T, cudaStream_t s) {
   if (T <= 0) return 0;

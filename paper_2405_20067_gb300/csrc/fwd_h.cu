@@ -126,8 +126,10 @@ __global__ void __launch_bounds__(416, 1) fwd_h_kernel(FwdArgs a) {
   __shared__ __align__(16) int sflag[CS][4];
   __shared__ int s_abort;
 
+  // tile of this CTA (a tile list selects a subset; surplus CTAs leave at once)
+  if (a.tiles && (int)blockIdx.x >= *a.n_tiles) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const long long t = blockIdx.x;
+  const long long t = a.tiles ? (long long)a.tiles[blockIdx.x] : (long long)blockIdx.x;
   const long long qt = t * a.tile;
   const int nq = (int)(a.Q - qt < a.tile ? a.Q - qt : a.tile);
   const int nh = nq > 128 ? 2 : 1;  // row blocks with queries
@@ -223,9 +225,10 @@ __global__ void __launch_bounds__(416, 1) fwd_h_kernel(FwdArgs a) {
       const int g = (i < nchunks && c < end) ? a.ids[c] : -1;
       return ((unsigned)g < (unsigned)a.Ge) ? g : -1;
     };
+    const int stride4 = a.rec_stride4 > 0 ? a.rec_stride4 : R4;
     auto load = [&](int g, float4 (&r)[R4]) {
       if (g >= 0) {
-        const float4* src = reinterpret_cast<const float4*>(a.rec) + (size_t)g * R4;
+        const float4* src = reinterpret_cast<const float4*>(a.rec) + (size_t)g * stride4;
 #pragma unroll
         for (int k = 0; k < R4; ++k) r[k] = __ldg(src + k);
       } else {

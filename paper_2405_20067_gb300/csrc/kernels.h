@@ -47,6 +47,10 @@ struct FwdArgs {
   int Ge;
   float* y;                  // [Q][3]
   int* status;               // device status word (timeouts of bounded waits)
+  int rec_stride4;           // float4s per record (0: the kernel's own record size)
+  int mat_off4;              // FP32 form: float4 offset of M inside a record (0: M first)
+  const int* tiles;          // null: CTA b is tile b; else CTA b < *n_tiles is tile tiles[b]
+  const int* n_tiles;
 };
 
 struct BwdArgs {
@@ -113,6 +117,8 @@ int launch_prep(int N, const PrepArgs& a, cudaStream_t s);
 int launch_cull_tile(int KP, const CullTileArgs& a, long long T, cudaStream_t s);
 int launch_permute_keys(const uint8_t* src, const int32_t* sorted, int n, int KP, uint8_t* dst,
                         cudaStream_t s);
+int launch_tile_split(const long long* offsets, long long T, long long min_cand, int* la, int* lb,
+                      int* n_a, int* n_b, cudaStream_t s);
 int launch_fwd(int N, const FwdArgs& a, long long T, cudaStream_t s);
 int launch_fwd_tc(int N, const FwdArgs& a, long long T, cudaStream_t s);  // FP16 hi/lo, N <= 12
 int launch_bwd_h(int N, const BwdArgs& a, long long T, cudaStream_t s);   // N <= 6

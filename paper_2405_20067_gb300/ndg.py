@@ -25,6 +25,13 @@ NDG_OK = 0
 NDG_ERR_CAPACITY = 2
 NDG_MODE_FP32 = 0
 NDG_MODE_TC = 1
+NDG_MODE_AUTO = 2  # forward: tensor cores on tiles with >= auto_min_candidates(N) candidates
+
+
+def auto_min_candidates(N: int) -> int:
+    """NDG_AUTO_MIN_CANDIDATES(N) of the header."""
+    return 192 if N <= 6 else 128
+
 MAX_N, MAX_K, MAX_BUCKETS, MAX_TILE = 12, 32, 255, 256
 _P = ctypes.c_void_p
 

@@ -88,3 +88,18 @@ def test_invalid_arguments_rejected_on_host(ndg):
     assert L.ndg_forward(ctypes.byref(m), ctypes.byref(q), ctypes.byref(cull), 7,
                          ctypes.c_void_p(0x7000), ws, BIG, None, None) == 1  # unknown mode
     assert L.ndg_loss_l2(-1, None, None, None, None, ws, BIG, None, None) == 1
+
+
+def test_mode_constants_match_header(ndg):
+    """The binding's mode numbers and AUTO threshold are the header's."""
+    import os
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "include", "ndg.h")).read()
+    defs = dict(re.findall(r"#define\s+(NDG_[A-Z_0-9]+)\s+(\d+)", src))
+    assert int(defs["NDG_MODE_FP32"]) == ndg.NDG_MODE_FP32
+    assert int(defs["NDG_MODE_TC"]) == ndg.NDG_MODE_TC
+    assert int(defs["NDG_MODE_AUTO"]) == ndg.NDG_MODE_AUTO
+    m = re.search(r"#define\s+NDG_AUTO_MIN_CANDIDATES\(N\)\s+\(\(N\) <= (\d+) \? (\d+) : (\d+)\)", src)
+    lim, lo, hi = (int(v) for v in m.groups())
+    for N in range(1, 13):
+        assert ndg.auto_min_candidates(N) == (lo if N <= lim else hi), N

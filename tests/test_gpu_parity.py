@@ -311,3 +311,33 @@ def test_value_at_mean_exact(ndg):
     a = np.float64(mix["alpha_raw"][0])
     c = 1.0 / (1.0 + np.exp(-mix["color_raw"][0].astype(np.float64)))
     np.testing.assert_allclose(y, np.exp(a) * c, rtol=1e-6)
+
+
+def test_auto_forward_picks_form_per_tile(ndg, oracle):
+    """NDG_MODE_AUTO: tiles with at least NDG_AUTO_MIN_CANDIDATES(N) candidates
+    get the tensor-core form, the others the FP32 form; each tile's outputs
+    equal that form's bit for bit, and all are within the tensor-core
+    tolerance of the oracle.  The Gaussians crowd one corner of the box so
+    that the tiles' candidate counts span both sides of the threshold."""
+    N, G, Q, tile, k = 6, 4000, 30000, 256, 16
+    seed = 640
+    mix, _, x = make_case(N, G, Q, seed)
+    mix = dict(mix)
+    mix["mean"] = (0.2 * (mix["mean"] + 1.0) - 1.0).astype(np.float32)  # means in [-1, -0.6]^6
+    gm, xt, proj, cp, ev, E = gpu_setup(ndg, N, mix, None, x, tile, k, 1 / 255, 3.0, 64, seed)
+    counts = np.diff(ev.cull.offsets.cpu().numpy())
+    dense = counts >= ndg.auto_min_candidates(N)
+    assert dense.any() and (~dense).any(), (counts.min(), counts.max())
+    y_tc = ev.forward(gm, mode=ndg.NDG_MODE_TC).cpu().numpy()
+    y_fp = ev.forward(gm, mode=ndg.NDG_MODE_FP32).cpu().numpy()
+    y_au = ev.forward(gm, mode=ndg.NDG_MODE_AUTO).cpu().numpy()
+    rows_dense = np.repeat(dense, tile)[:Q]
+    assert np.array_equal(y_au[rows_dense], y_tc[rows_dense])
+    assert np.array_equal(y_au[~rows_dense], y_fp[~rows_dense])
+    raw = oracle_raw(oracle, mix)
+    L, m, w = oracle.activate(raw)
+    offs, ids = oracle.cull_contract(L, m, w, x.astype(np.float64), tile, proj, 1 / 255, 3.0, 64)
+    yo = oracle.eval(L, m, w, x.astype(np.float64), tile, offs, ids)
+    worst = assert_outputs_close(y_au, yo, rtol=1e-3, floor=1e-3, what="auto forward")
+    print(f"auto: {int(dense.sum())} of {dense.size} tiles on the tensor cores, worst {worst:.2e}")
+    assert ndg.read_status(ev.ws) == 0
