@@ -15,6 +15,7 @@ Functions and the passages they follow (paper sections / equations):
   cull_contract   the FP32 bucket contract that makes candidate lists
                   reproducible bit for bit (conservative w.r.t. cull_exact)
   loss_l2, grad   plain L2 loss and the analytic gradient (Section 4.1)
+  loss_rel_l2     the relative L2 loss (Section 4.1; reading: (y - t)^2 / (y^2 + eps))
   adam            Adam update (the paper does not name its optimiser)
   densify         Section 3.3 materialisation of child Gaussians
 """
@@ -60,6 +61,7 @@ def _load():
         lib.oracle_cull_exact.restype = None
         lib.oracle_cull_contract.restype = ctypes.c_longlong
         lib.oracle_loss_l2.restype = ctypes.c_double
+        lib.oracle_loss_rel_l2.restype = ctypes.c_double
         lib.oracle_grad.restype = None
         lib.oracle_adam.restype = None
         lib.oracle_densify.restype = ctypes.c_int
@@ -218,6 +220,18 @@ def loss_l2(y, target):
     t, pt = _d(target)
     gbar = np.zeros_like(y)
     loss = lib.oracle_loss_l2(ctypes.c_longlong(y.shape[0]), py, pt, gbar.ctypes.data_as(_D))
+    return loss, gbar
+
+
+def loss_rel_l2(y, target, eps=1e-2):
+    """(loss, gbar [Q,3]) for the relative L2 loss: squared errors divided by
+    y^2 + eps (the denominator held constant for the gradient)."""
+    lib = _load()
+    y, py = _d(y)
+    t, pt = _d(target)
+    gbar = np.zeros_like(y)
+    loss = lib.oracle_loss_rel_l2(ctypes.c_longlong(y.shape[0]), py, pt, ctypes.c_double(eps),
+                                  gbar.ctypes.data_as(_D))
     return loss, gbar
 
 

@@ -358,6 +358,24 @@ double oracle_loss_l2(long long Q, const double* y, const double* target,
   return Q > 0 ? acc / n : 0.0;
 }
 
+/* Relative L2.  Section 4.1 trains with a relative L2 loss (after
+ * Noise2Noise) without printing it; the reading taken here: each squared
+ * error is divided by the square of the output itself plus eps, and the
+ * denominator is held constant when differentiating:
+ *   l = sum (y - t)^2 / (y^2 + eps) / (3Q),
+ *   dl/dy = 2 (y - t) / (y^2 + eps) / (3Q). */
+double oracle_loss_rel_l2(long long Q, const double* y, const double* target,
+                          double eps, double* gbar) {
+  double acc = 0.0, n = 3.0 * (double)Q;
+  for (long long i = 0; i < 3 * Q; ++i) {
+    double d = y[i] - target[i];
+    double den = y[i] * y[i] + eps;
+    acc += d * d / den;
+    if (gbar) gbar[i] = 2.0 * d / den / n;
+  }
+  return Q > 0 ? acc / n : 0.0;
+}
+
 /* Is g in the sorted candidate list of tile t (dense when offsets == NULL)? */
 static int in_tile(long long t, int g, const long long* offsets, const int* ids) {
   if (!offsets) return 1;

@@ -414,6 +414,37 @@ def test_loss_gradient_by_differences(oracle):
             assert abs(fd - gbar[i, c]) < 1e-10
 
 
+def test_relative_l2_closed_form_and_gradient(oracle):
+    """Relative L2 (Section 4.1, reading (y - t)^2 / (y^2 + eps) with the
+    denominator held constant): a hand-computed two-output example, the
+    eps -> 0 limit (squared relative error), invariance under scaling y, t by
+    s with eps by s^2, and dl/dy by central differences of the loss with the
+    denominator frozen at the unperturbed outputs."""
+    # Q = 1: y = (1, 2, 0), t = (0, 1, 1), eps = 1:
+    # (1/2 + 1/5 + 1/1) / 3 = 1.7 / 3;  gbar = 2 d / den / 3 = (1/3, 2/15, -2/3)
+    y = np.array([[1.0, 2.0, 0.0]])
+    t = np.array([[0.0, 1.0, 1.0]])
+    l0, g0 = oracle.loss_rel_l2(y, t, eps=1.0)
+    assert abs(l0 - 1.7 / 3.0) < 1e-15
+    np.testing.assert_allclose(g0, [[1.0 / 3.0, 2.0 / 15.0, -2.0 / 3.0]], rtol=1e-14)
+    r = np.random.default_rng(5)
+    y = r.uniform(0.5, 2.0, size=(9, 3))
+    t = r.uniform(0.0, 2.0, size=(9, 3))
+    l1, _ = oracle.loss_rel_l2(y, t, eps=0.0)
+    assert abs(l1 - np.mean(((y - t) / y) ** 2)) < 1e-14
+    ls, _ = oracle.loss_rel_l2(7.0 * y, 7.0 * t, eps=49.0 * 1e-2)
+    lr, gr = oracle.loss_rel_l2(y, t, eps=1e-2)
+    assert abs(ls - lr) < 1e-14 * abs(lr) + 1e-16
+    den = y ** 2 + 1e-2  # frozen denominator
+    f = lambda yy: np.sum((yy - t) ** 2 / den) / y.size
+    for i in range(9):
+        for c in range(3):
+            yp, ym = y.copy(), y.copy()
+            yp[i, c] += 1e-3
+            ym[i, c] -= 1e-3
+            assert abs((f(yp) - f(ym)) / 2e-3 - gr[i, c]) < 1e-11
+
+
 def _fd_check(oracle, raw, x, target, tile, offs, ids, n_samples, seed, h=1e-3, rtol=2e-5):
     y = oracle.eval(*oracle.activate(raw), x, tile, offs, ids)
     _, gbar = oracle.loss_l2(y, target)
