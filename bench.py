@@ -394,6 +394,81 @@ def run_fit(form: str, steps: int, warmup: int, device: str, flush, world: int, 
     return res
 
 
+def run_ablation(device) -> dict:
+    """The paper's culling ablations in shape (Section 3.2 and its
+    evaluation): for an N = 6 fit workload (20,000 Gaussians, 2^18
+    Morton-tiled queries) the fixed-k_sigma sweep (average candidates per
+    tile, FP32 forward time, largest dropped contribution against the unculled
+    evaluation), the contribution-cutoff mode, and culling on / off for
+    inference (tensor-core forward) and for training (50 Adam steps)."""
+    import torch
+    from paper_2405_20067_gb300 import ndg, synth
+    from paper_2405_20067_gb300.train import Trainer
+    N, Gs, Qs, k = 6, 20_000, 1 << 18, 16
+    c = synth.config1(G=Gs, Q=Qs)
+    gm = ndg.Mixture.from_arrays(N, c["mix"], G_cap=Gs, device=device)
+    x = torch.as_tensor(c["x"]).to(device)
+    target = torch.as_tensor(c["target"]).to(device)
+    proj = torch.as_tensor(c["proj"]).to(device)
+    T = (Qs + TILE - 1) // TILE
+
+    def timed(fn, reps=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def evaluator(cp):
+        ev = ndg.Evaluator(gm, x, TILE, cp, backward=False)
+        E = ev.build(gm)
+        return ev, E
+
+    dense_cp = ndg.CullParams(0, None, 0.0, 3.0, 1)
+    ev_d, E_d = evaluator(dense_cp)
+    y_dense = ev_d.forward(gm, mode=ndg.NDG_MODE_FP32).clone()
+    ymax = float(y_dense.abs().max())
+    rows = []
+    settings = [("k_sigma", ks, 0.0) for ks in (1.0, 1.5, 2.0, 2.5, 3.0, 4.0, 5.0)]
+    settings.append(("cutoff 1/255", 3.0, CUTOFF))
+    for name, ks, cut in settings:
+        cp = ndg.CullParams(k, proj, cut, ks, BUCKETS)
+        ev, E = evaluator(cp)
+        y = ev.forward(gm, mode=ndg.NDG_MODE_FP32)
+        drop = float((y_dense - y).abs().max())
+        ms = timed(lambda: ev.forward(gm, mode=ndg.NDG_MODE_FP32))
+        rows.append({"mode": name, "k_sigma": ks, "cutoff": cut, "avg_candidates": E / T,
+                     "fraction_of_dense": E / E_d, "max_dropped": drop,
+                     "max_dropped_rel": drop / ymax, "fp32_forward_ms": round(ms, 4)})
+    cull_cp = ndg.CullParams(k, proj, CUTOFF, 3.0, BUCKETS)
+    ev_c, E_c = evaluator(cull_cp)
+    inf = {"tc_forward_ms_culled": round(timed(lambda: ev_c.forward(gm, mode=ndg.NDG_MODE_TC)), 4),
+           "tc_forward_ms_dense": round(timed(lambda: ev_d.forward(gm, mode=ndg.NDG_MODE_TC)), 4),
+           "cull_build_ms": round(timed(lambda: ev_c.build(gm)), 4)}
+    train = {}
+    for name, cp in (("culled", cull_cp), ("dense", dense_cp)):
+        mix = ndg.Mixture.from_arrays(N, c["mix"], G_cap=Gs, device=device)
+        tr = Trainer(mix, x, target, TILE, cp, lr=1e-3, t=0.01, phase=0,
+                     mode=ndg.NDG_MODE_TC, bwd_mode=ndg.NDG_MODE_TC)
+        first = float(tr.step(refine=False).item())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(50):
+            tr.step(refine=False)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / 50 * 1e3
+        assert tr.check() == ndg.NDG_OK
+        train[name] = {"ms_per_step": round(dt, 3), "loss_first": first,
+                       "loss_after_50": float(tr.loss.item())}
+    return {"workload": f"N=6, {Gs} Gaussians, 2^18 Morton-tiled queries, tile {TILE}, k={k}",
+            "dense_entries": E_d, "sweep": rows, "inference": inf, "training": train}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -410,6 +485,9 @@ def main():
                     help="time eager steps instead of replays of the CUDA-graph-captured step")
     ap.add_argument("--workload", default="fit_n6", choices=sorted(WORKLOADS),
                     help="fit_n6: the headline workload; small_n6: 1/8 of it for profiling")
+    ap.add_argument("--ablation", action="store_true",
+                    help="only the culling ablations (k_sigma sweep, culling on / off); one "
+                         "JSON line")
     args = ap.parse_args()
     global G, Q
     G, Q = WORKLOADS[args.workload]
@@ -427,6 +505,10 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device(device))
     from paper_2405_20067_gb300 import build
     build.build()
+    if args.ablation:
+        if rank == 0:
+            print(json.dumps({"ablation": run_ablation(device)}))
+        return
     peaks, peak_kind = load_peaks()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)  # > 129 MB L2
     chosen = run_fit("tc", args.steps, args.warmup, device, flush, world,

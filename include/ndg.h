@@ -173,6 +173,18 @@ ndg_status ndg_loss_l2(long long Q, const float* y, const float* target,
                        float* dy, double* loss_dev, void* ws, size_t ws_bytes,
                        ndg_stream stream, ndg_trace* trace);
 
+/* Relative L2 loss.  Section 4.1 trains with a relative L2 loss (after
+ * Noise2Noise) without printing its form; the reading implemented:
+ *   loss = sum (y - target)^2 / (y^2 + eps) / (3Q) written to loss_dev [1]
+ *   (FP64), dy = 2 (y - target) / (y^2 + eps) / (3Q)  [Q][3],
+ * the denominator treated as a constant when differentiating (no gradient
+ * flows through it).  eps > 0 (finite), e.g. 1e-2; otherwise
+ * NDG_ERR_INVALID_ARG.  Deterministic reduction; same workspace use as
+ * ndg_loss_l2. */
+ndg_status ndg_loss_rel_l2(long long Q, const float* y, const float* target,
+                           float eps, float* dy, double* loss_dev, void* ws,
+                           size_t ws_bytes, ndg_stream stream, ndg_trace* trace);
+
 /* Analytic gradient of the loss through Eq. 1, 2, 6-8 given dy = dl/dy
  * [Q][3]: writes dl/d(raw parameter) into `grad` (same layout and N, G,
  * has_children as mix; rows >= G untouched).  Recomputes everything from

@@ -408,6 +408,22 @@ ndg_status ndg_loss_l2(long long Q, const float* y, const float* target, float* 
   return cuda_ok();
 }
 
+ndg_status ndg_loss_rel_l2(long long Q, const float* y, const float* target, float eps, float* dy,
+                           double* loss_dev, void* ws, size_t ws_bytes, ndg_stream stream,
+                           ndg_trace* trace) {
+  if (Q < 0 || !loss_dev || (Q > 0 && (!y || !target || !dy))) return NDG_ERR_INVALID_ARG;
+  if (!(eps > 0.0f) || !std::isfinite(eps)) return NDG_ERR_INVALID_ARG;
+  if (!ws || !aligned(ws, kAlign)) return NDG_ERR_INVALID_ARG;
+  const size_t off = align_up(sizeof(WsHeader));
+  if (ws_bytes < off + kLossParts * sizeof(double)) return NDG_ERR_WORKSPACE;
+  double* part = (double*)((char*)ws + off);
+  Tracer tr(trace, (cudaStream_t)stream);
+  tr.begin();
+  tr += launch_loss(y, target, dy, 3 * Q, part, loss_dev, (cudaStream_t)stream, (double)eps);
+  tr.end();
+  return cuda_ok();
+}
+
 ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q, const ndg_cull* cull,
                         int mode, const float* dy, ndg_mixture* grad, void* ws, size_t ws_bytes,
                         ndg_stream stream, ndg_trace* trace) {

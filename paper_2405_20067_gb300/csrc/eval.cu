@@ -150,17 +150,23 @@ __global__ void __launch_bounds__(128) fwd_kernel(FwdArgs a) {
 // ---- loss ---------------------------------------------------------------------
 constexpr int LOSS_BLOCKS = 512;
 
+// Plain L2 (rel_eps < 0): d^2 and dy = scale d.  Relative L2 (rel_eps >= 0,
+// Section 4.1's relative L2 read as d^2 / (y^2 + eps) with the denominator
+// held constant): d^2 / den and dy = scale d / den.  Per-block partial sums
+// in FP64, combined in a fixed order by loss_final_kernel.
 __global__ void __launch_bounds__(256) loss_kernel(const float* __restrict__ y,
                                                    const float* __restrict__ target,
                                                    float* __restrict__ dy, long long n, double scale,
-                                                   double* __restrict__ part) {
+                                                   double rel_eps, double* __restrict__ part) {
   __shared__ double sh[256];
   double acc = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const double d = (double)y[i] - (double)target[i];
-    dy[i] = (float)(d * scale);
-    acc += d * d;
+    const double yi = (double)y[i];
+    const double d = yi - (double)target[i];
+    const double den = rel_eps >= 0.0 ? yi * yi + rel_eps : 1.0;
+    dy[i] = (float)(d * scale / den);
+    acc += d * d / den;
   }
   sh[threadIdx.x] = acc;
   __syncthreads();
@@ -648,9 +654,9 @@ int launch_fwd(int N, const FwdArgs& a, long long T, cudaStream_t s) {
 }
 
 int launch_loss(const float* y, const float* target, float* dy, long long n, double* part,
-                double* loss, cudaStream_t s) {
+                double* loss, cudaStream_t s, double rel_eps) {
   const double scale = n > 0 ? 2.0 / (double)n : 0.0;
-  loss_kernel<<<LOSS_BLOCKS, 256, 0, s>>>(y, target, dy, n, scale, part);
+  loss_kernel<<<LOSS_BLOCKS, 256, 0, s>>>(y, target, dy, n, scale, rel_eps, part);
   loss_final_kernel<<<1, LOSS_BLOCKS, 0, s>>>(part, n, loss);
   return 2;
 }

@@ -123,7 +123,7 @@ int launch_fwd(int N, const FwdArgs& a, long long T, cudaStream_t s);
 int launch_fwd_tc(int N, const FwdArgs& a, long long T, cudaStream_t s);  // FP16 hi/lo, N <= 12
 int launch_bwd_h(int N, const BwdArgs& a, long long T, cudaStream_t s);   // N <= 6
 int launch_loss(const float* y, const float* target, float* dy, long long n, double* part,
-                 double* loss, cudaStream_t s);
+                double* loss, cudaStream_t s, double rel_eps = -1.0);
 int launch_bwd(int N, const BwdArgs& a, long long T, cudaStream_t s);
 int launch_segsum(const float* part, int RP, const long long* goff, int Ge, const int32_t* perm,
                  float* gsum, cudaStream_t s);

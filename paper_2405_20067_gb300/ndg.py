@@ -93,7 +93,8 @@ def _tr(trace):
     return ctypes.byref(trace.c) if trace is not None else None
 
 
-EXPORTS = ["ndg_workspace_size", "ndg_build_cull", "ndg_forward", "ndg_loss_l2", "ndg_backward",
+EXPORTS = ["ndg_workspace_size", "ndg_build_cull", "ndg_forward", "ndg_loss_l2", "ndg_loss_rel_l2",
+           "ndg_backward",
            "ndg_adam", "ndg_densify", "ndg_read_status", "ndg_status_string", "ndg_version",
            "ndg_forward_noalloc"]
 NDG_ERR_SCRATCH_LIMIT = 7
@@ -116,6 +117,8 @@ def lib():
         L.ndg_build_cull.argtypes = [M, Qp, CP, C, _P, sz, _P, TR]
         L.ndg_forward.argtypes = [M, Qp, C, ctypes.c_int, _P, _P, sz, _P, TR]
         L.ndg_loss_l2.argtypes = [ctypes.c_longlong, _P, _P, _P, _P, _P, sz, _P, TR]
+        L.ndg_loss_rel_l2.argtypes = [ctypes.c_longlong, _P, _P, ctypes.c_float, _P, _P, _P, sz,
+                                      _P, TR]
         L.ndg_backward.argtypes = [M, Qp, C, ctypes.c_int, _P, M, _P, sz, _P, TR]
         L.ndg_adam.argtypes = [M, M, M, M, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                ctypes.c_float, _P, TR]
@@ -125,7 +128,8 @@ def lib():
         L.ndg_status_string.argtypes = [ctypes.c_int]
         L.ndg_status_string.restype = ctypes.c_char_p
         L.ndg_version.restype = ctypes.c_int
-        for name in ["ndg_build_cull", "ndg_forward", "ndg_loss_l2", "ndg_backward", "ndg_adam",
+        for name in ["ndg_build_cull", "ndg_forward", "ndg_loss_l2", "ndg_loss_rel_l2",
+                     "ndg_backward", "ndg_adam",
                      "ndg_densify", "ndg_read_status", "ndg_forward_noalloc"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -301,6 +305,15 @@ def loss_l2(y: torch.Tensor, target: torch.Tensor, dy: torch.Tensor, loss: torch
             ws: torch.Tensor, stream=None, trace: Trace | None = None):
     _check(lib().ndg_loss_l2(int(y.shape[0]), _ptr(y), _ptr(target), _ptr(dy), _ptr(loss),
                              _ptr(ws), ws.numel(), _stream(stream), _tr(trace)), "ndg_loss_l2")
+
+
+def loss_rel_l2(y: torch.Tensor, target: torch.Tensor, dy: torch.Tensor, loss: torch.Tensor,
+                ws: torch.Tensor, eps: float = 1e-2, stream=None, trace: Trace | None = None):
+    """Relative L2: sum (y - t)^2 / (y^2 + eps) / (3Q), dy with the
+    denominator held constant."""
+    _check(lib().ndg_loss_rel_l2(int(y.shape[0]), _ptr(y), _ptr(target), float(eps), _ptr(dy),
+                                 _ptr(loss), _ptr(ws), ws.numel(), _stream(stream), _tr(trace)),
+           "ndg_loss_rel_l2")
 
 
 def backward(mix: Mixture, x: torch.Tensor, tile: int, cull: Cull, dy: torch.Tensor,

@@ -61,10 +61,14 @@ class Trainer:
     def __init__(self, mix: ndg.Mixture, x: torch.Tensor, target: torch.Tensor, tile: int,
                  cp: ndg.CullParams, lr: float = 1e-3, t: float = 0.01, phase: int = 300,
                  E_cap: int | None = None, seed: int = 0, mode: int = ndg.NDG_MODE_FP32,
-                 bwd_mode: int | None = None):
+                 bwd_mode: int | None = None, loss: str = "l2", rel_eps: float = 1e-2):
         """mode / bwd_mode: NDG_MODE_FP32 or NDG_MODE_TC for the forward and
         the backward (the tensor-core backward covers N <= 6); bwd_mode
-        defaults to mode."""
+        defaults to mode.  loss: "l2" (plain) or "rel_l2" (the relative L2 of
+        Section 4.1, squared errors over y^2 + rel_eps)."""
+        if loss not in ("l2", "rel_l2"):
+            raise ValueError(f"unknown loss {loss!r}")
+        self.loss_kind, self.rel_eps = loss, rel_eps
         self.mix, self.tile, self.cp, self.mode = mix, tile, cp, mode
         self.bwd_mode = mode if bwd_mode is None else bwd_mode
         self.lr, self.t, self.phase = lr, t, phase
@@ -121,8 +125,12 @@ class Trainer:
                        trace=self._tr("build_cull"))
         with torch.enable_grad():
             y = evaluate(self.ev, mix)
-            ndg.loss_l2(y.detach(), self.target, self.dy, self.loss, self.ev.ws,
-                        trace=self._tr("loss"))
+            if self.loss_kind == "rel_l2":
+                ndg.loss_rel_l2(y.detach(), self.target, self.dy, self.loss, self.ev.ws,
+                                eps=self.rel_eps, trace=self._tr("loss"))
+            else:
+                ndg.loss_l2(y.detach(), self.target, self.dy, self.loss, self.ev.ws,
+                            trace=self._tr("loss"))
             y.backward(self.dy)
         grad = ndg.Mixture(mix.N, mix.G, *[getattr(mix, f).grad if getattr(mix, f) is not None
                                            else None for f in _PARAMS],

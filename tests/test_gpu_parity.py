@@ -184,6 +184,46 @@ def test_loss_matches_oracle(ndg, oracle):
     assert_outputs_close(dy.cpu().numpy(), go, rtol=1e-6, floor=1e-12)
 
 
+def test_relative_loss_matches_oracle(ndg, oracle):
+    """Relative L2 (Section 4.1 reading): loss to 1e-12, dy to 1e-6, with
+    outputs near zero (where the eps term dominates) included."""
+    import torch
+    r = synth.rng(6)
+    Q = 50003
+    y = r.uniform(0, 2, (Q, 3)).astype(np.float32)
+    y[:100] *= 1e-3
+    t = r.uniform(0, 2, (Q, 3)).astype(np.float32)
+    yt, tt = torch.as_tensor(y).cuda(), torch.as_tensor(t).cuda()
+    dy = torch.empty_like(yt)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ws = ndg.workspace(1 << 16)
+    for eps in (1e-2, 0.5):
+        ndg.loss_rel_l2(yt, tt, dy, loss, ws, eps=eps)
+        lo, go = oracle.loss_rel_l2(y.astype(np.float64), t.astype(np.float64),
+                                    eps=float(np.float32(eps)))
+        assert abs(loss.item() - lo) <= 1e-12 * lo
+        assert_outputs_close(dy.cpu().numpy(), go, rtol=1e-6, floor=1e-12)
+
+
+def test_fit_with_relative_loss_reduces_it(ndg):
+    """The trainer's relative-L2 option drives the same graph-capturable step."""
+    import torch
+    from paper_2405_20067_gb300.train import Trainer
+    N, G, Q = 6, 400, 8192
+    mix = synth.mixture(N, G, 90)
+    gm = ndg.Mixture.from_arrays(N, mix, G_cap=2 * G)
+    x = torch.as_tensor(synth.queries_box(N, Q, 91)).cuda()
+    target = torch.as_tensor(synth.targets_uniform(Q, 92)).cuda()
+    cp = ndg.CullParams(8, torch.as_tensor(synth.projections(N, 8, 93)).cuda(), 1 / 255, 3.0, 64)
+    tr = Trainer(gm, x, target, 256, cp, lr=1e-2, t=0.01, phase=0, loss="rel_l2")
+    first = float(tr.step(refine=False).item())
+    for _ in range(40):
+        tr.step(refine=False)
+    last = float(tr.loss.item())
+    assert tr.check() == ndg.NDG_OK
+    assert last < 0.9 * first, (first, last)
+
+
 def test_adam_matches_oracle(ndg, oracle):
     import torch
     N, G = 6, 500
