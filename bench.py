@@ -469,6 +469,49 @@ def run_ablation(device) -> dict:
             "dense_entries": E_d, "sweep": rows, "inference": inf, "training": train}
 
 
+def run_render_batch(device, n_frames: int = 64) -> dict:
+    """Batched render (64 frame specs: G log-uniform in [1e4, 5e5], N in
+    {6, 8, 10}, 256^2 .. 1920 x 1080 pixels, one query per pixel, dims beyond
+    position uniform): per-frame latency of cull + forward (CUDA events, one
+    untimed frame first) with the autotuned configuration, p50 / p99 over
+    the frames, next to the fixed configuration (tensor cores, 256-query
+    tiles).  Frames run one after another; each frame's tiles spread over
+    every SM (one CTA per tile)."""
+    import numpy as np
+    import torch
+    from paper_2405_20067_gb300 import ndg, synth
+    from paper_2405_20067_gb300.render import Autotuner, Frame, frame_class
+    specs = synth.config4_frames(n=n_frames)
+    tuner = Autotuner()
+    rows = []
+    for f in specs:
+        N, G, W, H, sd = f["N"], f["G"], f["W"], f["H"], f["seed"]
+        gm = ndg.Mixture.from_arrays(N, synth.mixture(N, G, sd), device=device)
+        x = torch.as_tensor(synth.queries_frame(N, W, H, sd + 1)).to(device)
+        proj = torch.as_tensor(synth.projections(N, K_PROJ, sd + 2)).to(device)
+        fr = Frame(gm, x, ndg.CullParams(K_PROJ, proj, CUTOFF, 3.0, BUCKETS))
+        key = frame_class(N, G, W * H)
+        tuned_now = key not in tuner.cache
+        cfg = tuner.choose(key, fr.time)
+        ms = fr.time(cfg)
+        ms_fixed = fr.time(("tc", 256))
+        rows.append({"N": N, "G": G, "W": W, "H": H, "config": f"{cfg[0]}/{cfg[1]}",
+                     "tuned_here": tuned_now, "ms": round(ms, 4), "ms_tc256": round(ms_fixed, 4)})
+        fr.release()
+        del fr, gm, x
+        torch.cuda.empty_cache()
+    ms = np.array([r["ms"] for r in rows])
+    fx = np.array([r["ms_tc256"] for r in rows])
+    return {"frames": len(rows), "classes_tuned": len(tuner.cache),
+            "candidates": [f"{a}/{b}" for a, b in tuner.candidates],
+            "p50_ms": round(float(np.percentile(ms, 50)), 4),
+            "p99_ms": round(float(np.percentile(ms, 99)), 4),
+            "mean_ms": round(float(ms.mean()), 4),
+            "fixed_tc256_p50_ms": round(float(np.percentile(fx, 50)), 4),
+            "fixed_tc256_p99_ms": round(float(np.percentile(fx, 99)), 4),
+            "pixels": int(sum(r["W"] * r["H"] for r in rows)), "per_frame": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -485,6 +528,9 @@ def main():
                     help="time eager steps instead of replays of the CUDA-graph-captured step")
     ap.add_argument("--workload", default="fit_n6", choices=sorted(WORKLOADS),
                     help="fit_n6: the headline workload; small_n6: 1/8 of it for profiling")
+    ap.add_argument("--render-batch", action="store_true",
+                    help="only the batched render of 64 frame specs (autotuned launch "
+                         "configuration, p50 / p99 frame latency); one JSON line")
     ap.add_argument("--ablation", action="store_true",
                     help="only the culling ablations (k_sigma sweep, culling on / off); one "
                          "JSON line")
@@ -508,6 +554,10 @@ def main():
     if args.ablation:
         if rank == 0:
             print(json.dumps({"ablation": run_ablation(device)}))
+        return
+    if args.render_batch:
+        if rank == 0:
+            print(json.dumps({"render_batch": run_render_batch(device)}))
         return
     peaks, peak_kind = load_peaks()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)  # > 129 MB L2

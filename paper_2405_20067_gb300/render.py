@@ -1,0 +1,84 @@
+"""Frame rendering with an autotuned launch configuration.
+
+A frame is one query per pixel against one mixture: the cull (Section 3.2)
+and the forward (Eq. 1, Eq. 8) through the C ABI, nothing else.  The
+launch configuration of a frame -- the evaluation form (tensor cores, the
+per-tile automatic choice, or FP32) and the query-tile size (256 or 128
+queries: 16 x 16 or 16 x 8 pixels) -- is picked by `Autotuner`: the first
+frame of each class (N, G rounded to a power of two, pixel count rounded to
+a power of two) is rendered once with every candidate configuration, the
+fastest is kept for the class, and later frames of the class reuse it.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import torch
+
+from . import ndg
+
+#: candidate launch configurations: (form, queries per tile)
+CANDIDATES = (("tc", 256), ("auto", 256), ("tc", 128), ("fp32", 256))
+_MODES = {"tc": ndg.NDG_MODE_TC, "auto": ndg.NDG_MODE_AUTO, "fp32": ndg.NDG_MODE_FP32}
+
+
+def frame_class(N: int, G: int, Q: int) -> tuple:
+    """Frames of one class share a tuned configuration."""
+    return (N, int(round(math.log2(max(G, 1)))), int(round(math.log2(max(Q, 1)))))
+
+
+@dataclass
+class Autotuner:
+    candidates: tuple = CANDIDATES
+    cache: dict = field(default_factory=dict)
+    trials: dict = field(default_factory=dict)
+
+    def choose(self, key: tuple, time_config) -> tuple:
+        """time_config(cfg) -> ms of one frame; tried once per class."""
+        if key not in self.cache:
+            times = {cfg: time_config(cfg) for cfg in self.candidates}
+            self.trials[key] = times
+            self.cache[key] = min(times, key=times.get)
+        return self.cache[key]
+
+
+class Frame:
+    """One frame's device state: mixture, queries, cull buffers and
+    workspace per tile size (built lazily), output."""
+
+    def __init__(self, mix: ndg.Mixture, x: torch.Tensor, cp: ndg.CullParams):
+        self.mix, self.x, self.cp = mix, x, cp
+        self.Q = int(x.shape[0])
+        self.y = torch.empty(self.Q, 3, dtype=torch.float32, device=x.device)
+        self._ev = {}
+
+    def evaluator(self, tile: int) -> ndg.Evaluator:
+        if tile not in self._ev:
+            ev = ndg.Evaluator(self.mix, self.x, tile, self.cp, backward=False)
+            ev.build(self.mix)  # sizes the candidate buffers (synchronises once)
+            self._ev[tile] = ev
+        return self._ev[tile]
+
+    def render(self, cfg: tuple) -> torch.Tensor:
+        """Cull + forward on the current stream, no synchronisation."""
+        form, tile = cfg
+        ev = self.evaluator(tile)
+        ndg.build_cull(self.mix, self.x, tile, self.cp, ev.cull, ev.ws)
+        ndg.forward(self.mix, self.x, tile, ev.cull, self.y, ev.ws, mode=_MODES[form])
+        return self.y
+
+    def time(self, cfg: tuple, reps: int = 1) -> float:
+        """ms of one frame (CUDA events on the current stream, after one
+        untimed frame)."""
+        self.render(cfg)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            self.render(cfg)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def release(self):
+        self._ev.clear()
