@@ -248,6 +248,16 @@ ndg_status ndg_densify(ndg_mixture* mix, float a_thr, float a_child0,
 ndg_status ndg_forward_noalloc(const ndg_mixture* mix, const ndg_queries* q,
                                const ndg_cull* cull, float* y, ndg_stream stream);
 
+/* Failure-detection self-test of the bounded device waits: launches one
+ * CTA that waits on an mbarrier nothing ever completes, with the wait the
+ * tensor-core kernels use (which = 0: the sleeping warp wait, about a
+ * second; which = 1: the spinning wait of their final drain, about a second
+ * or two).  When the bound runs out it records NDG_ERR_TIMEOUT in the
+ * workspace status word (read with ndg_read_status) and returns; nothing
+ * faults and the context stays usable.  ws: any workspace (only its status
+ * word is used). */
+ndg_status ndg_selftest_timeout(int which, void* ws, size_t ws_bytes, ndg_stream stream);
+
 /* Synchronises `stream`, copies the workspace status word to *device_status
  * (an ndg_status value) and clears it. */
 ndg_status ndg_read_status(void* ws, ndg_stream stream, int* device_status);

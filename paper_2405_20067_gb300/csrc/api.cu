@@ -424,6 +424,13 @@ ndg_status ndg_loss_rel_l2(long long Q, const float* y, const float* target, flo
   return cuda_ok();
 }
 
+ndg_status ndg_selftest_timeout(int which, void* ws, size_t ws_bytes, ndg_stream stream) {
+  if (which != 0 && which != 1) return NDG_ERR_INVALID_ARG;
+  if (!ws || !aligned(ws, kAlign) || ws_bytes < sizeof(WsHeader)) return NDG_ERR_INVALID_ARG;
+  launch_selftest_wait(&reinterpret_cast<WsHeader*>(ws)->status, which, (cudaStream_t)stream);
+  return cuda_ok();
+}
+
 ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q, const ndg_cull* cull,
                         int mode, const float* dy, ndg_mixture* grad, void* ws, size_t ws_bytes,
                         ndg_stream stream, ndg_trace* trace) {

@@ -125,6 +125,7 @@ int launch_bwd_h(int N, const BwdArgs& a, long long T, cudaStream_t s);   // N <
 int launch_loss(const float* y, const float* target, float* dy, long long n, double* part,
                 double* loss, cudaStream_t s, double rel_eps = -1.0);
 int launch_bwd(int N, const BwdArgs& a, long long T, cudaStream_t s);
+int launch_selftest_wait(int* status, int which, cudaStream_t s);
 int launch_segsum(const float* part, int RP, const long long* goff, int Ge, const int32_t* perm,
                  float* gsum, cudaStream_t s);
 int launch_chain(int N, const ChainArgs& a, cudaStream_t s);

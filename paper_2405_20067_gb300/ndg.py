@@ -96,7 +96,7 @@ def _tr(trace):
 EXPORTS = ["ndg_workspace_size", "ndg_build_cull", "ndg_forward", "ndg_loss_l2", "ndg_loss_rel_l2",
            "ndg_backward",
            "ndg_adam", "ndg_densify", "ndg_read_status", "ndg_status_string", "ndg_version",
-           "ndg_forward_noalloc"]
+           "ndg_forward_noalloc", "ndg_selftest_timeout"]
 NDG_ERR_SCRATCH_LIMIT = 7
 
 
@@ -124,13 +124,15 @@ def lib():
                                ctypes.c_float, _P, TR]
         L.ndg_densify.argtypes = [M, ctypes.c_float, ctypes.c_float, _P, M, M, _P, _P, sz, _P, TR]
         L.ndg_forward_noalloc.argtypes = [M, Qp, C, _P, _P]
+        L.ndg_selftest_timeout.argtypes = [ctypes.c_int, _P, sz, _P]
         L.ndg_read_status.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_int)]
         L.ndg_status_string.argtypes = [ctypes.c_int]
         L.ndg_status_string.restype = ctypes.c_char_p
         L.ndg_version.restype = ctypes.c_int
         for name in ["ndg_build_cull", "ndg_forward", "ndg_loss_l2", "ndg_loss_rel_l2",
                      "ndg_backward", "ndg_adam",
-                     "ndg_densify", "ndg_read_status", "ndg_forward_noalloc"]:
+                     "ndg_densify", "ndg_read_status", "ndg_forward_noalloc",
+                     "ndg_selftest_timeout"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -305,6 +307,13 @@ def loss_l2(y: torch.Tensor, target: torch.Tensor, dy: torch.Tensor, loss: torch
             ws: torch.Tensor, stream=None, trace: Trace | None = None):
     _check(lib().ndg_loss_l2(int(y.shape[0]), _ptr(y), _ptr(target), _ptr(dy), _ptr(loss),
                              _ptr(ws), ws.numel(), _stream(stream), _tr(trace)), "ndg_loss_l2")
+
+
+def selftest_timeout(which: int, ws: torch.Tensor, stream=None):
+    """Bounded-wait self-test: a CTA waits on a barrier nothing completes and
+    records NDG_ERR_TIMEOUT in the workspace status word (read_status)."""
+    _check(lib().ndg_selftest_timeout(int(which), _ptr(ws), ws.numel(), _stream(stream)),
+           "ndg_selftest_timeout")
 
 
 def loss_rel_l2(y: torch.Tensor, target: torch.Tensor, dy: torch.Tensor, loss: torch.Tensor,

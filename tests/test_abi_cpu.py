@@ -88,6 +88,10 @@ def test_invalid_arguments_rejected_on_host(ndg):
     assert L.ndg_forward(ctypes.byref(m), ctypes.byref(q), ctypes.byref(cull), 7,
                          ctypes.c_void_p(0x7000), ws, BIG, None, None) == 1  # unknown mode
     assert L.ndg_loss_l2(-1, None, None, None, None, ws, BIG, None, None) == 1
+    assert L.ndg_loss_rel_l2(10, ctypes.c_void_p(0x7000), ctypes.c_void_p(0x8000), 0.0,
+                             ctypes.c_void_p(0x9000), ctypes.c_void_p(0xa000), ws, BIG, None,
+                             None) == 1  # eps must be > 0
+    assert L.ndg_selftest_timeout(2, ws, BIG, None) == 1  # unknown wait kind
 
 
 def test_mode_constants_match_header(ndg):
