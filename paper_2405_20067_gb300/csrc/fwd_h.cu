@@ -56,17 +56,24 @@ struct FwdHShape {
   static constexpr int KP = (F + 15) / 16 * 16;  // K step of kind::f16 is 16
   static constexpr int NC = 128;                 // candidates per chunk (MMA N)
   static constexpr int R = rec_floats(N);
-  static constexpr int CS = N <= 6 ? 4 : (N <= 8 ? 3 : 2);  // coefficient stages
   static constexpr uint32_t SBO = (KP / 8) * 128;  // 8-row group stride (bytes)
   static constexpr uint32_t PHI_BYTES = 256u * KP * 2;  // one of hi / lo, 256 rows
   static constexpr uint32_t HALF_BYTES = 128u * KP * 2; // one 128-row block
   static constexpr uint32_t B_BYTES = (uint32_t)NC * KP * 2;
   static constexpr uint32_t W_BYTES = (uint32_t)NC * 16;  // w0 w0' w1 w1' w2 w2' k k' per pair
   static constexpr uint32_t C_STAGE = 2 * B_BYTES + W_BYTES;
+  // coefficient stages: as many as fit next to Phi (at most 4; 2 KB are left
+  // for the static shared variables).  The builders run up to CS chunks ahead
+  // of the epilogue, which frees a stage only at the end of its chunk, so
+  // two stages leave the builders idle for a whole chunk (measured at N = 10:
+  // a third stage is worth about a fifth of the time).
+  static constexpr uint32_t STAGE_ROOM = 227u * 1024u - 2048u - 2 * PHI_BYTES - 128u;
+  static constexpr int CS = STAGE_ROOM / C_STAGE >= 4 ? 4 : (int)(STAGE_ROOM / C_STAGE);
   static constexpr uint32_t SMEM_USED = 2 * PHI_BYTES + CS * C_STAGE + 128;
   // more than half of the SM's shared memory: one CTA per SM
   static constexpr uint32_t SMEM = SMEM_USED > 116u * 1024u ? SMEM_USED : 116u * 1024u;
   static_assert(SMEM <= 227u * 1024u, "shared memory");
+  static_assert(CS >= 2, "coefficient stages");
   static_assert(NC == 128, "candidate mapping");
 };
 
