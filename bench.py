@@ -48,12 +48,12 @@ def workload_name(g, q):
 
 
 # DRAM bytes per candidate entry of one bwd_h_kernel<6> launch:
-# dram__bytes_read.sum + dram__bytes_write.sum = 19.91 MB + 298.04 MB from one
-# ncu capture of the 1/8 workload (E = 2,760,083 entries), i.e. 115.2 B per
-# entry; a full launch's traffic is this times its entries (the kernel streams
-# one gradient record per entry, so traffic grows in proportion).  To be
-# re-taken whenever the kernel changes.
-BWD_BYTES_PER_ENTRY = (19.909376e6 + 298.038784e6) / 2760083
+# dram__bytes_read.sum + dram__bytes_write.sum = 19.58 MB + 299.93 MB from one
+# ncu capture of the 1/8 workload (about 2.76 million entries), i.e. 115.8 B
+# per entry; a full launch's traffic is this times its entries (the kernel
+# streams one gradient record per entry, so traffic grows in proportion).  To
+# be re-taken whenever the kernel changes.
+BWD_BYTES_PER_ENTRY = (19.579904e6 + 299.926016e6) / 2760083
 
 
 def flops_per_pair(N: int):

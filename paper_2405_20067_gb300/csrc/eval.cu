@@ -154,6 +154,7 @@ constexpr int LOSS_BLOCKS = 512;
 // Section 4.1's relative L2 read as d^2 / (y^2 + eps) with the denominator
 // held constant): d^2 / den and dy = scale d / den.  Per-block partial sums
 // in FP64, combined in a fixed order by loss_final_kernel.
+template <bool REL>
 __global__ void __launch_bounds__(256) loss_kernel(const float* __restrict__ y,
                                                    const float* __restrict__ target,
                                                    float* __restrict__ dy, long long n, double scale,
@@ -164,9 +165,14 @@ __global__ void __launch_bounds__(256) loss_kernel(const float* __restrict__ y,
        i += (long long)gridDim.x * blockDim.x) {
     const double yi = (double)y[i];
     const double d = yi - (double)target[i];
-    const double den = rel_eps >= 0.0 ? yi * yi + rel_eps : 1.0;
-    dy[i] = (float)(d * scale / den);
-    acc += d * d / den;
+    if (REL) {  // one FP64 division per element (the FP64 rate is low here)
+      const double inv = 1.0 / (yi * yi + rel_eps);
+      dy[i] = (float)(d * scale * inv);
+      acc += d * d * inv;
+    } else {
+      dy[i] = (float)(d * scale);
+      acc += d * d;
+    }
   }
   sh[threadIdx.x] = acc;
   __syncthreads();
@@ -656,7 +662,10 @@ int launch_fwd(int N, const FwdArgs& a, long long T, cudaStream_t s) {
 int launch_loss(const float* y, const float* target, float* dy, long long n, double* part,
                 double* loss, cudaStream_t s, double rel_eps) {
   const double scale = n > 0 ? 2.0 / (double)n : 0.0;
-  loss_kernel<<<LOSS_BLOCKS, 256, 0, s>>>(y, target, dy, n, scale, rel_eps, part);
+  if (rel_eps >= 0.0)
+    loss_kernel<true><<<LOSS_BLOCKS, 256, 0, s>>>(y, target, dy, n, scale, rel_eps, part);
+  else
+    loss_kernel<false><<<LOSS_BLOCKS, 256, 0, s>>>(y, target, dy, n, scale, rel_eps, part);
   loss_final_kernel<<<1, LOSS_BLOCKS, 0, s>>>(part, n, loss);
   return 2;
 }
