@@ -13,7 +13,10 @@ Functions and the passages they follow (paper sections / equations):
   eval            Eq. 1 and Eq. 8 (dense or restricted to candidate lists)
   cull_exact      Section 3.2 Eq. 3-5, real-valued test in FP64
   cull_contract   the FP32 bucket contract that makes candidate lists
-                  reproducible bit for bit (conservative w.r.t. cull_exact)
+                  reproducible bit for bit (conservative w.r.t. cull_exact);
+                  optionally on position for Gaussians restricted to xc
+  condition       Section 3.2: a Gaussian restricted to constant inputs
+                  beyond position (completing the square in the precision)
   loss_l2, grad   plain L2 loss and the analytic gradient (Section 4.1)
   loss_rel_l2     the relative L2 loss (Section 4.1; reading: (y - t)^2 / (y^2 + eps))
   adam            Adam update (the paper does not name its optimiser)
@@ -60,6 +63,7 @@ def _load():
         lib.oracle_eval.restype = None
         lib.oracle_cull_exact.restype = None
         lib.oracle_cull_contract.restype = ctypes.c_longlong
+        lib.oracle_condition.restype = None
         lib.oracle_loss_l2.restype = ctypes.c_double
         lib.oracle_loss_rel_l2.restype = ctypes.c_double
         lib.oracle_grad.restype = None
@@ -179,13 +183,14 @@ def cull_exact(L, m, w, x, tile, proj, cutoff, k_sigma):
     return keep
 
 
-def cull_contract(L, m, w, x, tile, proj, cutoff, k_sigma, buckets, tiles=None):
+def cull_contract(L, m, w, x, tile, proj, cutoff, k_sigma, buckets, tiles=None, xc=None):
     """(offsets, ids [E] int32) from the FP32 bucket contract.
 
     tiles=None: every tile, offsets [T+1] int64.  Otherwise the lists of the
     given tile indices only (in that order), offsets [len(tiles)+1]; each list
     equals that tile's list in the full run (the ranges and keys still come
-    from the whole query set)."""
+    from the whole query set).  xc (N - 3 values): the contract on position
+    for the Gaussians restricted to the constant inputs xc (condition())."""
     lib = _load()
     L, pL = _d(L)
     m, pm = _d(m)
@@ -203,14 +208,33 @@ def cull_contract(L, m, w, x, tile, proj, cutoff, k_sigma, buckets, tiles=None):
         assert sel.size == 0 or (sel.min() >= 0 and sel.max() < T)
         n_sel, psel, nt = sel.size, sel.ctypes.data_as(_LL), sel.size
     offsets = np.zeros(nt + 1, dtype=np.int64)
+    if xc is not None:
+        xc, pxc = _d(np.asarray(xc, dtype=np.float64).reshape(N - 3))
+    else:
+        pxc = None
     args = (N, Ge, pL, pm, pw, ctypes.c_longlong(Q), px, tile, k, pp,
             ctypes.c_double(cutoff), ctypes.c_double(k_sigma), buckets,
-            ctypes.c_longlong(n_sel), psel)
+            ctypes.c_longlong(n_sel), psel, pxc)
     E = lib.oracle_cull_contract(*args, offsets.ctypes.data_as(_LL), None)
     ids = np.zeros(max(E, 1), dtype=np.int32)
     E2 = lib.oracle_cull_contract(*args, offsets.ctypes.data_as(_LL), ids.ctypes.data_as(_I))
     assert E2 == E
     return offsets, ids[:E]
+
+
+def condition(L, m, w, xc):
+    """Gaussians restricted to the constant inputs xc = (x_4 .. x_N):
+    (mu [Ge, 3], T [Ge, 3, 3] lower with covariance T^T T, wc [Ge, 3])."""
+    lib = _load()
+    L, pL = _d(L)
+    m, pm = _d(m)
+    w, pw = _d(w)
+    Ge, N = m.shape
+    xc, pxc = _d(np.asarray(xc, dtype=np.float64).reshape(N - 3))
+    mu, T, wc = np.zeros((Ge, 3)), np.zeros((Ge, 3, 3)), np.zeros((Ge, 3))
+    lib.oracle_condition(N, Ge, pL, pm, pw, pxc, mu.ctypes.data_as(_D), T.ctypes.data_as(_D),
+                         wc.ctypes.data_as(_D))
+    return mu, T, wc
 
 
 def loss_l2(y, target):

@@ -224,18 +224,112 @@ static int bucket_raw(float v, float lo, float inv_h, int B) {
   return (int)floorf(t);
 }
 
+/* Section 3.2: when every input beyond position is constant for an image,
+ * x_c = (x_4, .., x_N), each Gaussian restricted to x_c is a 3-D Gaussian
+ * over position.  With the precision A = V^-1 = M^T M (M = L^-1) split into
+ * the position block p (dims 0-2) and the rest c, completing the square gives
+ *   (x - m)^T A (x - m) = (x_p - mu)^T A_pp (x_p - mu) + q_c,
+ *   b = A_pc d_c, d_c = x_c - m_c, mu = m_p - A_pp^-1 b,
+ *   q_c = d_c^T A_cc d_c - b^T A_pp^-1 b,
+ * so the restriction is w exp(-q_c / 2) times a 3-D Gaussian with mean mu
+ * and covariance A_pp^-1 = T^T T, T = C^-1 for A_pp = C C^T (Cholesky).
+ * Per Gaussian g (N >= 4): mu [3], T [9] (row-major, lower), and the
+ * conditional weight wc [3] = w exp(-q_c / 2) with w the weights given. */
+void oracle_condition(int N, int Ge, const double* L, const double* m,
+                      const double* w, const double* xc, double* mu, double* T,
+                      double* wc) {
+#pragma omp parallel for schedule(static)
+  for (int g = 0; g < Ge; ++g) {
+    const double* Lg = L + (size_t)g * N * N;
+    const double* mg = m + (size_t)g * N;
+    double M[OMAXN * OMAXN], A[OMAXN * OMAXN];
+    /* M = L^-1 by forward substitution, column by column */
+    for (int j = 0; j < N; ++j) {
+      for (int i = 0; i < N; ++i) M[i * N + j] = 0.0;
+      M[j * N + j] = 1.0 / Lg[j * N + j];
+      for (int i = j + 1; i < N; ++i) {
+        double s = 0.0;
+        for (int k = j; k < i; ++k) s += Lg[i * N + k] * M[k * N + j];
+        M[i * N + j] = -s / Lg[i * N + i];
+      }
+    }
+    /* A = M^T M */
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < N; ++k) s += M[k * N + i] * M[k * N + j];
+        A[i * N + j] = s;
+      }
+    double dc[OMAXN], b[3];
+    for (int i = 3; i < N; ++i) dc[i] = xc[i - 3] - mg[i];
+    for (int i = 0; i < 3; ++i) {
+      double s = 0.0;
+      for (int k = 3; k < N; ++k) s += A[i * N + k] * dc[k];
+      b[i] = s;
+    }
+    /* Cholesky of A_pp (3 x 3): C lower with C C^T = A_pp */
+    double C[9];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j <= i; ++j) {
+        double s = A[i * N + j];
+        for (int k = 0; k < j; ++k) s -= C[i * 3 + k] * C[j * 3 + k];
+        C[i * 3 + j] = (i == j) ? sqrt(s) : s / C[j * 3 + j];
+      }
+    /* z = A_pp^-1 b: C y = b, C^T z = y */
+    double y3[3], z[3];
+    for (int i = 0; i < 3; ++i) {
+      double s = b[i];
+      for (int k = 0; k < i; ++k) s -= C[i * 3 + k] * y3[k];
+      y3[i] = s / C[i * 3 + i];
+    }
+    for (int i = 2; i >= 0; --i) {
+      double s = y3[i];
+      for (int k = i + 1; k < 3; ++k) s -= C[k * 3 + i] * z[k];
+      z[i] = s / C[i * 3 + i];
+    }
+    double qc = 0.0;
+    for (int i = 3; i < N; ++i) {
+      double s = 0.0;
+      for (int k = 3; k < N; ++k) s += A[i * N + k] * dc[k];
+      qc += dc[i] * s;
+    }
+    for (int i = 0; i < 3; ++i) qc -= b[i] * z[i];
+    const double f = exp(-0.5 * qc);
+    for (int i = 0; i < 3; ++i) {
+      mu[(size_t)g * 3 + i] = mg[i] - z[i];
+      wc[(size_t)g * 3 + i] = w[(size_t)g * 3 + i] * f;
+    }
+    /* T = C^-1 (lower) by forward substitution */
+    double* Tg = T + (size_t)g * 9;
+    for (int j = 0; j < 3; ++j) {
+      for (int i = 0; i < 3; ++i) Tg[i * 3 + j] = 0.0;
+      Tg[j * 3 + j] = 1.0 / C[j * 3 + j];
+      for (int i = j + 1; i < 3; ++i) {
+        double s = 0.0;
+        for (int k = j; k < i; ++k) s += C[i * 3 + k] * Tg[k * 3 + j];
+        Tg[i * 3 + j] = -s / C[i * 3 + i];
+      }
+    }
+  }
+}
+
 /* Runs the contract; writes the candidate lists as CSR (ascending ids per
  * tile).  ids may be NULL to count only.  Returns E, the total entries.
  * sel == NULL: every tile, offsets [T+1].  Otherwise only the n_sel tiles
  * listed in sel (in that order), offsets [n_sel+1]; the global per-projection
  * ranges and the keys are the same as for the whole query set, so each
- * selected tile's list equals its list in the full run. */
+ * selected tile's list equals its list in the full run.
+ * xc != NULL (N >= 4, the inputs beyond position constant, xc [N - 3]): the
+ * same contract on the position dims only, for the Gaussians restricted to
+ * xc (oracle_condition): a Gaussian's key uses mu, T and the conditional
+ * weight, rounded to FP32 (sigma_r = |T r|), and every projection and query
+ * enters with its first three components. */
 long long oracle_cull_contract(int N, int Ge, const double* L, const double* m,
                                const double* w, long long Q, const double* x,
                                int tile, int k, const double* proj,
                                double cutoff, double k_sigma, int B,
                                long long n_sel, const long long* sel,
-                               long long* offsets, int* ids) {
+                               const double* xc, long long* offsets, int* ids) {
   long long T = (Q + tile - 1) / tile;
   float* xf = (float*)malloc(sizeof(float) * (size_t)(Q * N + 1));
   float* rf = (float*)malloc(sizeof(float) * (size_t)(k * N + 1));
@@ -247,11 +341,23 @@ long long oracle_cull_contract(int N, int Ge, const double* L, const double* m,
   int* tk = (int*)malloc(sizeof(int) * (size_t)T * (2 * k + 1));
   for (long long i = 0; i < Q * N; ++i) xf[i] = (float)x[i];
   for (long long i = 0; i < (long long)k * N; ++i) rf[i] = (float)proj[i];
+  const int ND = xc ? 3 : N;  /* dims that enter the projections */
+  double *cmu = NULL, *cT = NULL, *cw = NULL;
+  if (xc) {
+    double* wr = (double*)malloc(sizeof(double) * (size_t)Ge * 3 + 8);
+    cmu = (double*)malloc(sizeof(double) * (size_t)Ge * 3 + 8);
+    cT = (double*)malloc(sizeof(double) * (size_t)Ge * 9 + 8);
+    cw = (double*)malloc(sizeof(double) * (size_t)Ge * 3 + 8);
+    /* the conditional weight starts from the FP32 weights, as the key does */
+    for (long long i = 0; i < (long long)Ge * 3; ++i) wr[i] = (double)(float)w[i];
+    oracle_condition(N, Ge, L, m, wr, xc, cmu, cT, cw);
+    free(wr);
+  }
   for (int j = 0; j < k; ++j) {
     lo[j] = INFINITY;
     hi[j] = -INFINITY;
     for (long long q = 0; q < Q; ++q) {
-      float v = dotf(N, xf + q * N, rf + (size_t)j * N);
+      float v = dotf(ND, xf + q * N, rf + (size_t)j * N);
       qv[q * k + j] = v;
       if (v < lo[j]) lo[j] = v;
       if (v > hi[j]) hi[j] = v;
@@ -264,21 +370,35 @@ long long oracle_cull_contract(int N, int Ge, const double* L, const double* m,
   for (int g = 0; g < Ge; ++g) {
     int* key = gk + (size_t)g * (2 * k + 1);
     float Lf[OMAXN * OMAXN], mf[OMAXN], wf[3];
-    for (int i = 0; i < N * N; ++i) Lf[i] = (float)L[(size_t)g * N * N + i];
-    for (int i = 0; i < N; ++i) mf[i] = (float)m[(size_t)g * N + i];
     double wd[3];
-    for (int c = 0; c < 3; ++c) { wf[c] = (float)w[(size_t)g * 3 + c]; wd[c] = wf[c]; }
+    if (xc) {  /* the position-only Gaussian: mean mu, factor T^T, weight wc */
+      for (int i = 0; i < 9; ++i) Lf[i] = (float)cT[(size_t)g * 9 + i];
+      for (int i = 0; i < 3; ++i) mf[i] = (float)cmu[(size_t)g * 3 + i];
+      for (int c = 0; c < 3; ++c) { wf[c] = (float)cw[(size_t)g * 3 + c]; wd[c] = wf[c]; }
+    } else {
+      for (int i = 0; i < N * N; ++i) Lf[i] = (float)L[(size_t)g * N * N + i];
+      for (int i = 0; i < N; ++i) mf[i] = (float)m[(size_t)g * N + i];
+      for (int c = 0; c < 3; ++c) { wf[c] = (float)w[(size_t)g * 3 + c]; wd[c] = wf[c]; }
+    }
     double kgd = cull_radius(wd, (double)(float)cutoff, (double)(float)k_sigma);
     key[0] = kgd >= 0.0;
     float kg = (float)kgd;
     for (int j = 0; key[0] && j < k; ++j) {
       const float* r = rf + (size_t)j * N;
-      float mr = dotf(N, mf, r);
+      float mr = dotf(ND, mf, r);
       float s2 = 0.0f;
-      for (int c = 0; c < N; ++c) {
-        float tc = 0.0f;
-        for (int i = c; i < N; ++i) tc = fmaf(Lf[i * N + c], r[i], tc);
-        s2 = fmaf(tc, tc, s2);
+      if (xc) {  /* sigma_r^2 = |T r|^2, T lower (row-major 3 x 3) */
+        for (int i = 0; i < 3; ++i) {
+          float tc = 0.0f;
+          for (int c = 0; c <= i; ++c) tc = fmaf(Lf[i * 3 + c], r[c], tc);
+          s2 = fmaf(tc, tc, s2);
+        }
+      } else {
+        for (int c = 0; c < N; ++c) {
+          float tc = 0.0f;
+          for (int i = c; i < N; ++i) tc = fmaf(Lf[i * N + c], r[i], tc);
+          s2 = fmaf(tc, tc, s2);
+        }
       }
       float sr = sqrtf(s2);
       float ks = kg * sr;
@@ -341,6 +461,7 @@ long long oracle_cull_contract(int N, int Ge, const double* L, const double* m,
   if (offsets)
     for (long long i = 0; i <= nt; ++i) offsets[i] = cnt[i];
   free(cnt);
+  free(cmu); free(cT); free(cw);
   free(xf); free(rf); free(qv); free(lo); free(hi); free(ih); free(gk); free(tk);
   return E;
 }

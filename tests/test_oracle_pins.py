@@ -278,6 +278,70 @@ def test_cull_contract_tile_selection_matches_full_run(oracle):
     assert eo.tolist() == [0] and ei.size == 0
 
 
+def test_condition_reproduces_the_nd_gaussian(oracle):
+    """Section 3.2 conditioning: each Gaussian restricted to the constant
+    inputs xc equals wc exp(-1/2 (x_p - mu)^T (T^T T)^-1 (x_p - mu)) at every
+    position (checked against the N-D evaluation of that Gaussian alone, with
+    the 3 x 3 inverse taken by numpy), and a diagonal factor gives the closed
+    form mu = m_p, T = diag(L_pp) (covariance diag(L_pp^2)),
+    wc = w exp(-1/2 sum ((xc - m_c) / L_cc)^2)."""
+    N = 6
+    mix = synth.mixture(N, 40, seed=21)
+    ch = synth.children(N, 40, 22, spread=0.2)
+    L, m, w = oracle.activate(raw_from(oracle, mix, ch))
+    r = np.random.default_rng(23)
+    xc = r.uniform(-0.5, 0.5, size=N - 3)
+    mu, T, wc = oracle.condition(L, m, w, xc)
+    xp = r.uniform(-1.0, 1.0, size=(50, 3))
+    x = np.concatenate([xp, np.repeat(xc[None, :], 50, axis=0)], axis=1)
+    for g in range(m.shape[0]):
+        y = oracle.eval(L[g:g + 1], m[g:g + 1], w[g:g + 1], x, tile=50)
+        V3 = T[g].T @ T[g]
+        d = xp - mu[g]
+        e = np.exp(-0.5 * np.einsum("qi,ij,qj->q", d, np.linalg.inv(V3), d))
+        np.testing.assert_allclose(y, wc[g][None, :] * e[:, None], rtol=1e-9, atol=1e-300)
+        assert np.allclose(np.triu(T[g], 1), 0.0)
+    # diagonal factor
+    Ld = np.diag([0.3, 0.5, 0.2, 0.4, 0.25, 0.6])[None]
+    md = np.array([[0.1, -0.2, 0.3, 0.0, 0.5, -0.4]])
+    wd = np.array([[0.7, 0.2, 1.3]])
+    mu, T, wc = oracle.condition(Ld, md, wd, xc)
+    np.testing.assert_allclose(mu[0], md[0, :3], rtol=1e-14)
+    np.testing.assert_allclose(T[0], np.diag(np.diag(Ld[0])[:3]), rtol=1e-14)
+    f = np.exp(-0.5 * np.sum(((xc - md[0, 3:]) / np.diag(Ld[0])[3:]) ** 2))
+    np.testing.assert_allclose(wc[0], wd[0] * f, rtol=1e-14)
+
+
+def test_conditioned_cull_is_sound(oracle):
+    """The contract on position for the Gaussians restricted to xc drops a
+    (tile, Gaussian) pair only if the N-D Gaussian's largest weight times its
+    factor stays below the cutoff at every query of the tile (queries carry
+    xc in their last N - 3 inputs); the lists are much shorter than the
+    contract's on all N inputs."""
+    N, G, Q, tile, k = 6, 300, 2048, 64, 8
+    mix = synth.mixture(N, G, seed=31)
+    L, m, w = oracle.activate(raw_from(oracle, mix))
+    r = np.random.default_rng(32)
+    xc = r.uniform(-0.5, 0.5, size=N - 3)
+    xp = synth.queries_box(3, Q, 33).astype(np.float64)
+    x = np.concatenate([xp, np.repeat(xc[None, :], Q, axis=0)], axis=1)
+    proj = synth.projections(N, k, 34)
+    cutoff = 1.0 / 255.0
+    offs, ids = oracle.cull_contract(L, m, w, x, tile, proj, cutoff, 3.0, 64, xc=xc)
+    offs_n, _ = oracle.cull_contract(L, m, w, x, tile, proj, cutoff, 3.0, 64)
+    assert offs[-1] < 0.5 * offs_n[-1]
+    T = offs.size - 1
+    keep = np.zeros((T, G), dtype=bool)
+    for t in range(T):
+        keep[t, ids[offs[t]:offs[t + 1]]] = True
+    A = np.linalg.inv(L @ np.transpose(L, (0, 2, 1)))
+    for g in range(G):
+        d = x - m[g]
+        s = np.einsum("qi,ij,qj->q", d, A[g], d).reshape(T, tile)
+        contrib = w[g].max() * np.exp(-0.5 * s)
+        assert np.all(contrib[~keep[:, g]] < cutoff), g
+
+
 def _raw_single_rows(N, means, thetas, alphas, gammas):
     return {"mean": np.asarray(means, np.float64).reshape(-1, N),
             "theta": np.asarray(thetas, np.float64).reshape(len(alphas), -1),
