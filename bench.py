@@ -465,8 +465,41 @@ def run_ablation(device) -> dict:
         assert tr.check() == ndg.NDG_OK
         train[name] = {"ms_per_step": round(dt, 3), "loss_first": first,
                        "loss_after_50": float(tr.loss.item())}
+    # Section 3.2's easy case: the inputs beyond position constant for a frame
+    # (N = 10, 500,000 Gaussians, one 1920 x 1080 frame): the cull on all
+    # inputs against the cull on position for the Gaussians restricted to
+    # the constants
+    del ev_d, ev_c
+    torch.cuda.empty_cache()
+    Nr = RENDER["N"]
+    mixr = synth.mixture(Nr, RENDER["G"], 2)
+    gr = ndg.Mixture.from_arrays(Nr, mixr, device=device)
+    xf = synth.queries_frame(Nr, RENDER["W"], RENDER["H"], 3)
+    xcn = synth.rng(5).uniform(-1.0, 1.0, size=Nr - 3).astype(xf.dtype)
+    xf[:, 3:] = xcn
+    xr = torch.as_tensor(xf).to(device)
+    xc = torch.as_tensor(xcn).to(device)
+    cpr = ndg.CullParams(RENDER["k"], torch.as_tensor(synth.projections(Nr, RENDER["k"], 4)).to(device),
+                         CUTOFF, 3.0, RENDER["buckets"])
+    cond = {}
+    for name, xcv in (("all inputs", None), ("conditioned on position", xc)):
+        ev = ndg.Evaluator(gr, xr, TILE, cpr, E_cap=1 << 24, backward=False)
+        E = ev.build(gr, xc=xcv)
+
+        def frame():
+            if xcv is None:
+                ndg.build_cull(gr, xr, TILE, cpr, ev.cull, ev.ws)
+            else:
+                ndg.build_cull_conditioned(gr, xr, TILE, cpr, xcv, ev.cull, ev.ws)
+            ev.forward(gr, mode=ndg.NDG_MODE_TC)
+
+        cond[name] = {"entries": E, "frame_ms": round(timed(frame, reps=3), 3)}
+        del ev
+        torch.cuda.empty_cache()
     return {"workload": f"N=6, {Gs} Gaussians, 2^18 Morton-tiled queries, tile {TILE}, k={k}",
-            "dense_entries": E_d, "sweep": rows, "inference": inf, "training": train}
+            "dense_entries": E_d, "sweep": rows, "inference": inf, "training": train,
+            "constant_inputs_frame": {"workload": "N=10, 500,000 Gaussians, 1920 x 1080, "
+                                                  "inputs beyond position constant", **cond}}
 
 
 def run_render_batch(device, n_frames: int = 64) -> dict:

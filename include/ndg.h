@@ -140,6 +140,24 @@ ndg_status ndg_build_cull(const ndg_mixture* mix, const ndg_queries* q,
                           const ndg_cull_params* cp, ndg_cull* out, void* ws,
                           size_t ws_bytes, ndg_stream stream, ndg_trace* trace);
 
+/* Section 3.2, the case of inputs beyond position constant for an image:
+ * the same lists as ndg_build_cull, but each Gaussian is first restricted to
+ * the constant inputs xc = (x_4 .. x_N) [N - 3] (device pointer): with the
+ * precision A = (L L^T)^-1 split into position (first three inputs) and the
+ * rest, completing the square turns it into a 3-D Gaussian over position
+ * with weight w exp(-q_c / 2) (q_c = d_c^T A_cc d_c - b^T A_pp^-1 b,
+ * b = A_pc d_c, d_c = xc - m_c), mean m_p - A_pp^-1 b and covariance A_pp^-1.
+ * Keys, cutoff radius and tile bounds then use position only: the first
+ * three entries of each projection and of each query (the caller's queries
+ * must carry xc in their other inputs; they are not read).  The lists are
+ * exactly those of the contract on the restricted Gaussians and are usually
+ * far shorter than on all N inputs.  N >= 4, else NDG_ERR_INVALID_ARG;
+ * evaluation (ndg_forward / ndg_backward) is unchanged. */
+ndg_status ndg_build_cull_conditioned(const ndg_mixture* mix, const ndg_queries* q,
+                                      const ndg_cull_params* cp, const float* xc,
+                                      ndg_cull* out, void* ws, size_t ws_bytes,
+                                      ndg_stream stream, ndg_trace* trace);
+
 #define NDG_MODE_FP32 0 /* centred form z = L^{-1}(x - m) on the FP32 pipe */
 #define NDG_MODE_TC 1   /* lifted quadratic form on the tensor cores: s =
                            phi(x - c) . coef with phi = [x x^T (lower), x, 1]

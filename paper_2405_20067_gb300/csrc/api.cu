@@ -258,13 +258,18 @@ size_t ndg_workspace_size(const ndg_mixture* mix, const ndg_queries* q,
   return need;
 }
 
-ndg_status ndg_build_cull(const ndg_mixture* mix, const ndg_queries* q, const ndg_cull_params* cp,
-                          ndg_cull* out, void* ws, size_t ws_bytes, ndg_stream stream,
-                          ndg_trace* trace) {
+namespace {
+
+// The cull (Section 3.2); xc != null: on position, for the Gaussians
+// restricted to the constant inputs xc (ndg_build_cull_conditioned).
+ndg_status build_cull(const ndg_mixture* mix, const ndg_queries* q, const ndg_cull_params* cp,
+                      const float* xc, ndg_cull* out, void* ws, size_t ws_bytes,
+                      ndg_stream stream, ndg_trace* trace) {
   ndg_status st;
   if ((st = check_mix(mix)) || (st = check_queries(q)) || (st = check_cull_params(cp)) ||
       (st = check_cull(out)))
     return st;
+  if (xc && mix->N < 4) return NDG_ERR_INVALID_ARG;
   if (!ws || !aligned(ws, kAlign)) return NDG_ERR_INVALID_ARG;
   Sizes z = make_sizes(mix, q, cp, out->E_cap);
   CommonLayout c = common_layout(z);
@@ -281,7 +286,7 @@ ndg_status ndg_build_cull(const ndg_mixture* mix, const ndg_queries* q, const nd
   uint8_t* tkey = (uint8_t*)(w + L.tkey);
   uint8_t* gkey = (uint8_t*)(w + L.gkey);
   if (k > 0) {
-    tr += launch_tile_bounds(N, q->x, q->Q, q->tile_size, T, k, cp->proj, tb, s);
+    tr += launch_tile_bounds(N, q->x, q->Q, q->tile_size, T, k, cp->proj, tb, s, xc ? 3 : N);
     tr += launch_cull_range(tb, T, k, B, q->Q, range, s);
     tr += launch_tile_keys(tb, T, k, KP, B, range, tkey, s);
   }
@@ -296,6 +301,7 @@ ndg_status ndg_build_cull(const ndg_mixture* mix, const ndg_queries* q, const nd
   pa.gkey = k > 0 ? gkey : nullptr;
   pa.bin = (uint32_t*)(w + L.bin);
   pa.status = status;
+  pa.xc = xc;
   tr += launch_prep(N, pa, s);
   uint32_t* sk;
   int32_t* sv;
@@ -332,6 +338,22 @@ ndg_status ndg_build_cull(const ndg_mixture* mix, const ndg_queries* q, const nd
     tr.end();
   }
   return cuda_ok();
+}
+
+}  // namespace
+
+ndg_status ndg_build_cull(const ndg_mixture* mix, const ndg_queries* q, const ndg_cull_params* cp,
+                          ndg_cull* out, void* ws, size_t ws_bytes, ndg_stream stream,
+                          ndg_trace* trace) {
+  return build_cull(mix, q, cp, nullptr, out, ws, ws_bytes, stream, trace);
+}
+
+ndg_status ndg_build_cull_conditioned(const ndg_mixture* mix, const ndg_queries* q,
+                                      const ndg_cull_params* cp, const float* xc, ndg_cull* out,
+                                      void* ws, size_t ws_bytes, ndg_stream stream,
+                                      ndg_trace* trace) {
+  if (!xc) return NDG_ERR_INVALID_ARG;
+  return build_cull(mix, q, cp, xc, out, ws, ws_bytes, stream, trace);
 }
 
 ndg_status ndg_forward(const ndg_mixture* mix, const ndg_queries* q, const ndg_cull* cull, int mode,

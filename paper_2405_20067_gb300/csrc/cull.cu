@@ -28,7 +28,8 @@ namespace ndg {
 // ---- tile bounds ----------------------------------------------------------
 template <int N>
 __global__ void tile_bounds_kernel(const float* __restrict__ x, long long Q, int tile, long long T,
-                                   int k, const float* __restrict__ proj, float* __restrict__ tb) {
+                                   int k, const float* __restrict__ proj, float* __restrict__ tb,
+                                   int nd) {
   const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (t >= T) return;
@@ -42,7 +43,8 @@ __global__ void tile_bounds_kernel(const float* __restrict__ x, long long Q, int
     for (long long q = q0 + lane; q < q1; q += 32) {
       float acc = 0.0f;
 #pragma unroll
-      for (int d = 0; d < N; ++d) acc = __fmaf_rn(x[q * N + d], pj[d], acc);
+      for (int d = 0; d < N; ++d)
+        if (d < nd) acc = __fmaf_rn(x[q * N + d], pj[d], acc);  // nd = 3: position only
       lo = fminf(lo, acc);
       hi = fmaxf(hi, acc);
     }
@@ -125,6 +127,116 @@ __device__ __forceinline__ void act_lower64(const float* __restrict__ th, double
       double v = (double)th[tri(i) + j];
       L[tri(i) + j] = (i == j) ? exp(v) : 2.0 / (1.0 + exp(-v)) - 1.0;
     }
+}
+
+// Section 3.2 conditioning of one Gaussian on the constant inputs xc beyond
+// position, in FP64 with separately rounded products and sums (no fused
+// multiply-add), in the order of the plain definition: M = L^-1,
+// A = M^T M, d_c = xc - m_c, b = A_pc d_c, C C^T = A_pp (Cholesky),
+// z = A_pp^-1 b, q_c = d_c^T A_cc d_c - b^T z; the restriction is
+// wc = w exp(-q_c / 2) times a 3-D Gaussian with mean mu = m_p - z and
+// covariance T^T T, T = C^-1.  Outputs rounded once to FP32.
+template <int N>
+__device__ bool condition_gaussian(const double* L, const double* m, const float* wf,
+                                   const float* __restrict__ xc, float* muf, float* Tf, float* wcf) {
+  double M[N][N], A[N][N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) M[i][j] = 0.0;
+    M[j][j] = __ddiv_rn(1.0, L[tri(j) + j]);
+#pragma unroll
+    for (int i = j + 1; i < N; ++i) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = j; k < i; ++k) s = __dadd_rn(s, __dmul_rn(L[tri(i) + k], M[k][j]));
+      M[i][j] = __ddiv_rn(-s, L[tri(i) + i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < N; ++k) s = __dadd_rn(s, __dmul_rn(M[k][i], M[k][j]));
+      A[i][j] = s;
+    }
+  double dc[N], b[3];
+#pragma unroll
+  for (int i = 3; i < N; ++i) dc[i] = __dsub_rn((double)xc[i - 3], m[i]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 3; k < N; ++k) s = __dadd_rn(s, __dmul_rn(A[i][k], dc[k]));
+    b[i] = s;
+  }
+  double C[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      double s = A[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) s = __dsub_rn(s, __dmul_rn(C[i][k], C[j][k]));
+      C[i][j] = (i == j) ? __dsqrt_rn(s) : __ddiv_rn(s, C[j][j]);
+    }
+  double y3[3], z[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    double s = b[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) s = __dsub_rn(s, __dmul_rn(C[i][k], y3[k]));
+    y3[i] = __ddiv_rn(s, C[i][i]);
+  }
+#pragma unroll
+  for (int i = 2; i >= 0; --i) {
+    double s = y3[i];
+#pragma unroll
+    for (int k = i + 1; k < 3; ++k) s = __dsub_rn(s, __dmul_rn(C[k][i], z[k]));
+    z[i] = __ddiv_rn(s, C[i][i]);
+  }
+  double qc = 0.0;
+#pragma unroll
+  for (int i = 3; i < N; ++i) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 3; k < N; ++k) s = __dadd_rn(s, __dmul_rn(A[i][k], dc[k]));
+    qc = __dadd_rn(qc, __dmul_rn(dc[i], s));
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) qc = __dsub_rn(qc, __dmul_rn(b[i], z[i]));
+  const double f = exp(__dmul_rn(-0.5, qc));
+  bool finite = true;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    muf[i] = (float)__dsub_rn(m[i], z[i]);
+    wcf[i] = (float)__dmul_rn((double)wf[i], f);
+    finite &= isfinite(muf[i]) && isfinite(wcf[i]);
+  }
+  double T[3][3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) T[i][j] = 0.0;
+    T[j][j] = __ddiv_rn(1.0, C[j][j]);
+#pragma unroll
+    for (int i = j + 1; i < 3; ++i) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = j; k < i; ++k) s = __dadd_rn(s, __dmul_rn(C[i][k], T[k][j]));
+      T[i][j] = __ddiv_rn(-s, C[i][i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Tf[i * 3 + j] = (float)T[i][j];
+      finite &= isfinite(Tf[i * 3 + j]);
+    }
+  return finite;
 }
 
 template <int N>
@@ -237,12 +349,18 @@ __global__ void __launch_bounds__(128) prep_kernel(PrepArgs a) {
   }
 
   if (a.gkey || a.bin) {
-    // Cull radius: k_sigma, or sqrt(2 ln(w_max / cutoff)) from the FP32
-    // weights in FP64, rounded once.
-    float kg;
+    // conditioned keys: the Gaussian restricted to the constant inputs
+    float cmu[3], cT[9], cw[3];
+    const bool cond = a.xc != nullptr;
     bool live = finite;
+    if constexpr (N >= 4) {
+      if (cond) live = live && condition_gaussian<N>(L, m, wf, a.xc, cmu, cT, cw);
+    }
+    // Cull radius: k_sigma, or sqrt(2 ln(w_max / cutoff)) from the FP32
+    // weights (conditioned: the conditional weights) in FP64, rounded once.
+    float kg;
     if (a.cutoff > 0.0f) {
-      float wm = fmaxf(fmaxf(wf[0], wf[1]), wf[2]);
+      float wm = cond ? fmaxf(fmaxf(cw[0], cw[1]), cw[2]) : fmaxf(fmaxf(wf[0], wf[1]), wf[2]);
       if (wm > a.cutoff) kg = (float)sqrt(2.0 * log((double)wm / (double)a.cutoff));
       else { kg = -1.0f; live = false; }
     } else {
@@ -255,16 +373,27 @@ __global__ void __launch_bounds__(128) prep_kernel(PrepArgs a) {
       float rr[N];
 #pragma unroll
       for (int d = 0; d < N; ++d) rr[d] = r[d];
-      float mr = 0.0f;
+      float mr = 0.0f, s2 = 0.0f;
+      if (cond) {  // position only: m_r = mu . r, sigma_r^2 = |T r|^2
 #pragma unroll
-      for (int d = 0; d < N; ++d) mr = __fmaf_rn(mf[d], rr[d], mr);
-      float s2 = 0.0f;
+        for (int d = 0; d < 3; ++d) mr = __fmaf_rn(cmu[d], rr[d], mr);
 #pragma unroll
-      for (int c = 0; c < N; ++c) {
-        float tc = 0.0f;
+        for (int i = 0; i < 3; ++i) {
+          float tc = 0.0f;
 #pragma unroll
-        for (int i = c; i < N; ++i) tc = __fmaf_rn(Lf[tri(i) + c], rr[i], tc);
-        s2 = __fmaf_rn(tc, tc, s2);
+          for (int c = 0; c <= i; ++c) tc = __fmaf_rn(cT[i * 3 + c], rr[c], tc);
+          s2 = __fmaf_rn(tc, tc, s2);
+        }
+      } else {
+#pragma unroll
+        for (int d = 0; d < N; ++d) mr = __fmaf_rn(mf[d], rr[d], mr);
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+          float tc = 0.0f;
+#pragma unroll
+          for (int i = c; i < N; ++i) tc = __fmaf_rn(Lf[tri(i) + c], rr[i], tc);
+          s2 = __fmaf_rn(tc, tc, s2);
+        }
       }
       const float sr = __fsqrt_rn(s2);
       const float ks = __fmul_rn(kg, sr);
@@ -437,10 +566,11 @@ __global__ void permute_keys_kernel(const uint8_t* __restrict__ src, const int32
   }
 
 int launch_tile_bounds(int N, const float* x, long long Q, int tile, long long T, int k,
-                       const float* proj, float* tb, cudaStream_t s) {
+                       const float* proj, float* tb, cudaStream_t s, int nd) {
   if (T <= 0 || k <= 0) return 0;
+  if (nd <= 0 || nd > N) nd = N;
   unsigned blocks = (unsigned)ceil_div<long long>(T * 32, 256);
-#define L_TB(n) tile_bounds_kernel<n><<<blocks, 256, 0, s>>>(x, Q, tile, T, k, proj, tb)
+#define L_TB(n) tile_bounds_kernel<n><<<blocks, 256, 0, s>>>(x, Q, tile, T, k, proj, tb, nd)
   NDG_SWITCH_N(N, L_TB)
 #undef L_TB
   return 1;

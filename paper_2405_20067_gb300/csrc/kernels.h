@@ -21,6 +21,10 @@ struct PrepArgs {
   uint8_t* gkey;       // [Ge][2 KP] or null
   uint32_t* bin;       // [Ge] or null
   int* status;
+  // Section 3.2 conditioning: when set, the inputs beyond position are the
+  // constants xc [N - 3] and the keys are those of each Gaussian restricted
+  // to them (position only); projections enter with their first 3 entries
+  const float* xc;
 };
 
 struct CullTileArgs {
@@ -108,7 +112,7 @@ struct DensifyArgs {
 };
 
 int launch_tile_bounds(int N, const float* x, long long Q, int tile, long long T, int k,
-                        const float* proj, float* tb, cudaStream_t s);
+                        const float* proj, float* tb, cudaStream_t s, int nd = 0);  // nd: dims used (0: N)
 int launch_cull_range(const float* tb, long long T, int k, int B, long long Q, float* range,
                        cudaStream_t s);
 int launch_tile_keys(const float* tb, long long T, int k, int KP, int B, const float* range,

@@ -93,7 +93,7 @@ def _tr(trace):
     return ctypes.byref(trace.c) if trace is not None else None
 
 
-EXPORTS = ["ndg_workspace_size", "ndg_build_cull", "ndg_forward", "ndg_loss_l2", "ndg_loss_rel_l2",
+EXPORTS = ["ndg_workspace_size", "ndg_build_cull", "ndg_build_cull_conditioned", "ndg_forward", "ndg_loss_l2", "ndg_loss_rel_l2",
            "ndg_backward",
            "ndg_adam", "ndg_densify", "ndg_read_status", "ndg_status_string", "ndg_version",
            "ndg_forward_noalloc", "ndg_selftest_timeout"]
@@ -115,6 +115,7 @@ def lib():
         L.ndg_workspace_size.argtypes = [M, Qp, CP, ctypes.c_longlong]
         L.ndg_workspace_size.restype = sz
         L.ndg_build_cull.argtypes = [M, Qp, CP, C, _P, sz, _P, TR]
+        L.ndg_build_cull_conditioned.argtypes = [M, Qp, CP, _P, C, _P, sz, _P, TR]
         L.ndg_forward.argtypes = [M, Qp, C, ctypes.c_int, _P, _P, sz, _P, TR]
         L.ndg_loss_l2.argtypes = [ctypes.c_longlong, _P, _P, _P, _P, _P, sz, _P, TR]
         L.ndg_loss_rel_l2.argtypes = [ctypes.c_longlong, _P, _P, ctypes.c_float, _P, _P, _P, sz,
@@ -129,7 +130,7 @@ def lib():
         L.ndg_status_string.argtypes = [ctypes.c_int]
         L.ndg_status_string.restype = ctypes.c_char_p
         L.ndg_version.restype = ctypes.c_int
-        for name in ["ndg_build_cull", "ndg_forward", "ndg_loss_l2", "ndg_loss_rel_l2",
+        for name in ["ndg_build_cull", "ndg_build_cull_conditioned", "ndg_forward", "ndg_loss_l2", "ndg_loss_rel_l2",
                      "ndg_backward", "ndg_adam",
                      "ndg_densify", "ndg_read_status", "ndg_forward_noalloc",
                      "ndg_selftest_timeout"]:
@@ -287,6 +288,20 @@ def build_cull(mix: Mixture, x: torch.Tensor, tile: int, cp: CullParams, cull: C
                                 _stream(stream), _tr(trace)), "ndg_build_cull")
 
 
+def build_cull_conditioned(mix: Mixture, x: torch.Tensor, tile: int, cp: CullParams,
+                           xc: torch.Tensor, cull: Cull, ws: torch.Tensor, stream=None,
+                           trace: Trace | None = None):
+    """The cull on position for the Gaussians restricted to the constant
+    inputs xc [N - 3] (device FP32), which the queries carry beyond position."""
+    assert xc.is_cuda and xc.dtype == torch.float32 and xc.numel() == mix.N - 3
+    _check(lib().ndg_build_cull_conditioned(ctypes.byref(mix.c()),
+                                            ctypes.byref(queries_c(x, tile)),
+                                            ctypes.byref(cp.c()), _ptr(xc),
+                                            ctypes.byref(cull.c()), _ptr(ws), ws.numel(),
+                                            _stream(stream), _tr(trace)),
+           "ndg_build_cull_conditioned")
+
+
 def forward(mix: Mixture, x: torch.Tensor, tile: int, cull: Cull, y: torch.Tensor,
             ws: torch.Tensor, mode: int = NDG_MODE_FP32, stream=None, trace: Trace | None = None):
     _check(lib().ndg_forward(ctypes.byref(mix.c()), ctypes.byref(queries_c(x, tile)),
@@ -388,9 +403,16 @@ class Evaluator:
         n = workspace_size(mix, self.x, self.tile, self.cp, self.E_cap if self.want_bwd else 0)
         self.ws = workspace(n, self.x.device)
 
-    def build(self, mix: Mixture, exact_capacity: bool = True) -> int:
-        """Builds the candidate lists; returns E (synchronises once)."""
-        build_cull(mix, self.x, self.tile, self.cp, self.cull, self.ws)
+    def build(self, mix: Mixture, exact_capacity: bool = True,
+              xc: torch.Tensor | None = None) -> int:
+        """Builds the candidate lists (conditioned on the constant inputs xc
+        when given); returns E (synchronises once)."""
+        def run():
+            if xc is None:
+                build_cull(mix, self.x, self.tile, self.cp, self.cull, self.ws)
+            else:
+                build_cull_conditioned(mix, self.x, self.tile, self.cp, xc, self.cull, self.ws)
+        run()
         E = self.cull.E()
         if E > self.E_cap:
             st = read_status(self.ws)
@@ -398,7 +420,7 @@ class Evaluator:
             self.E_cap = int(E * 1.25) + 1024
             self.cull = Cull(self.T, self.E_cap, str(self.x.device))
             self._alloc_ws(mix)
-            build_cull(mix, self.x, self.tile, self.cp, self.cull, self.ws)
+            run()
             E = self.cull.E()
         return E
 

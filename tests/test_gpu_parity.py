@@ -381,3 +381,38 @@ def test_auto_forward_picks_form_per_tile(ndg, oracle):
     worst = assert_outputs_close(y_au, yo, rtol=1e-3, floor=1e-3, what="auto forward")
     print(f"auto: {int(dense.sum())} of {dense.size} tiles on the tensor cores, worst {worst:.2e}")
     assert ndg.read_status(ev.ws) == 0
+
+
+@pytest.mark.parametrize("N,G,Q,tile,k,children", [(6, 3000, 20000, 256, 16, False),
+                                                   (10, 2000, 9000, 128, 8, True),
+                                                   (4, 500, 3000, 64, 4, False)])
+def test_conditioned_cull_bit_exact_and_forward(ndg, oracle, N, G, Q, tile, k, children):
+    """Section 3.2 with the inputs beyond position constant: the lists of
+    ndg_build_cull_conditioned equal the oracle's conditioned contract (same
+    sets per tile, bit-exact), are shorter than the unconditioned ones, and
+    the forward over them matches the oracle in both forms."""
+    import torch
+    seed = 700 + N
+    mix, ch, _ = make_case(N, G, 16, seed, children)
+    r = synth.rng(seed + 5)
+    xc = r.uniform(-0.5, 0.5, size=N - 3).astype(np.float32)
+    xp = synth.queries_box(3, Q, seed + 6)
+    x = np.concatenate([xp, np.repeat(xc[None, :], Q, axis=0)], axis=1).astype(np.float32)
+    gm, xt, proj, cp, ev, E_full = gpu_setup(ndg, N, mix, ch, x, tile, k, 1 / 255, 3.0, 64, seed)
+    E = ev.build(gm, xc=torch.as_tensor(xc).cuda())
+    assert E < E_full
+    raw = oracle_raw(oracle, mix, ch)
+    L, m, w = oracle.activate(raw)
+    xd = x.astype(np.float64)
+    offs, ids = oracle.cull_contract(L, m, w, xd, tile, proj, 1 / 255, 3.0, 64,
+                                     xc=xc.astype(np.float64))
+    assert E == offs[-1]
+    got = csr_sets(ev.cull.offsets.cpu().numpy(), ev.cull.ids[:E].cpu().numpy())
+    want = csr_sets(offs, ids)
+    assert all(np.array_equal(a, b) for a, b in zip(got, want))
+    yo = oracle.eval(L, m, w, xd, tile, offs, ids)
+    assert_outputs_close(ev.forward(gm, mode=ndg.NDG_MODE_FP32).cpu().numpy(), yo)
+    assert_outputs_close(ev.forward(gm, mode=ndg.NDG_MODE_TC).cpu().numpy(), yo, rtol=1e-3,
+                         floor=1e-3)
+    print(f"conditioned N={N}: E = {E} (unconditioned {E_full})")
+    assert ndg.read_status(ev.ws) == 0
