@@ -379,6 +379,7 @@ def run_fit(form: str, steps: int, warmup: int, device: str, flush, world: int, 
         th = target.cpu().pin_memory()
         e2e_ms = []
         for i in range(e2e_steps + 1):
+            flush.zero_()  # the same L2 flush as between the device-timed steps (untimed)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             loss = tr.step(xh, th, refine=False)
