@@ -416,3 +416,31 @@ def test_conditioned_cull_bit_exact_and_forward(ndg, oracle, N, G, Q, tile, k, c
                          floor=1e-3)
     print(f"conditioned N={N}: E = {E} (unconditioned {E_full})")
     assert ndg.read_status(ev.ws) == 0
+
+
+def test_config0_l2_loss_and_gradient(ndg, oracle):
+    """Config 0 as specified: N = 6, 1000 Gaussians, 16384 queries, no
+    culling, the plain L2 loss against a 200-Gaussian ground truth (its
+    values from the oracle), seed 0: loss and every raw-parameter gradient
+    of the FP32 path against the oracle."""
+    import torch
+    c = synth.config0()
+    N = c["N"]
+    x = c["x"].astype(np.float64)
+    Lg, mg, wg = oracle.activate(oracle_raw(oracle, c["gt"]))
+    target = oracle.eval(Lg, mg, wg, x).astype(np.float32)
+    gm, xt, proj, cp, ev, E = gpu_setup(ndg, N, c["mix"], None, c["x"], 256, 0, 0.0, 3.0, 1, 0)
+    y = ev.forward(gm)
+    dy = torch.empty_like(y)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ndg.loss_l2(y, torch.as_tensor(target).cuda(), dy, loss, ev.ws)
+    grad = ev.backward(gm, dy)
+    raw = oracle_raw(oracle, c["mix"])
+    L, m, w = oracle.activate(raw)
+    yo = oracle.eval(L, m, w, x)
+    lo, go = oracle.loss_l2(yo, target.astype(np.float64))
+    assert abs(loss.item() - lo) <= 1e-5 * lo
+    want = oracle.grad(raw, x, 256, None, None, go)
+    got = {n: getattr(grad, n)[:1000].cpu().numpy() for n in NAMES[:4]}
+    rep = assert_grads_close(got, want, NAMES[:4])
+    print("config 0: loss %.6e; " % loss.item() + " ".join(f"{n}={v:.1e}" for n, v in rep.items()))
