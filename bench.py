@@ -163,14 +163,14 @@ def build_workload(device):
 RENDER = {"N": 10, "G": 500_000, "W": 1920, "H": 1080, "k": 16, "buckets": 64}
 
 
-def render_n10_1080p(device, steps: int, warmup: int, flush):
+def render_n10_1080p(device, steps: int, warmup: int, flush, res: tuple | None = None):
     """Second metric: one 1920 x 1080 frame (16 x 16 pixel tiles, 8160 tiles,
     the last tile row half full) of 10-D surface queries against 500,000
     10-D Gaussians: cull + forward (S1-S4), ms per frame, for the lifted
     tensor-core form (the value) and the plain FP32 form."""
     import torch
     from paper_2405_20067_gb300 import ndg, synth
-    r = RENDER
+    r = dict(RENDER) if res is None else dict(RENDER, W=res[0], H=res[1])
     mix = synth.mixture(r["N"], r["G"], 2)
     gm = ndg.Mixture.from_arrays(r["N"], mix, device=device)
     x = torch.as_tensor(synth.queries_frame(r["N"], r["W"], r["H"], 3)).to(device)
@@ -628,6 +628,9 @@ def main():
     ap.add_argument("--render-batch", action="store_true",
                     help="only the batched render of 64 frame specs (autotuned launch "
                          "configuration, p50 / p99 frame latency); one JSON line")
+    ap.add_argument("--render-only", metavar="WxH", default=None,
+                    help="only the N = 10 render metric at this resolution (e.g. 480x272, a "
+                         "small frame for profiling); one JSON line")
     ap.add_argument("--fit-n10", action="store_true",
                     help="only the N = 10 fit with refinement (loss curve, G(t), wall time); "
                          "one JSON line")
@@ -654,6 +657,13 @@ def main():
     if args.ablation:
         if rank == 0:
             print(json.dumps({"ablation": run_ablation(device)}))
+        return
+    if args.render_only:
+        w_, h_ = (int(v) for v in args.render_only.lower().split("x"))
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+        if rank == 0:
+            print(json.dumps({"render": render_n10_1080p(device, max(3, args.steps // 4), args.warmup,
+                                                         flush, res=(w_, h_))}))
         return
     if args.fit_n10:
         if rank == 0:
