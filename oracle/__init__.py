@@ -42,23 +42,30 @@ _LL = ctypes.POINTER(ctypes.c_longlong)
 _U8 = ctypes.POINTER(ctypes.c_ubyte)
 
 
+def compile_source(src: str, out: str) -> str:
+    """gcc (OpenMP, no FP contraction) of one oracle source into a shared library."""
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    tmp = out + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-fPIC", "-shared", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (OpenMP, no FP contraction)."""
+    """Compile the oracle (skipped while the library is newer than the source)."""
     if not force and os.path.exists(_OUT) and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC):
         return _OUT
-    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-    tmp = _OUT + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _OUT)
-    return _OUT
+    return compile_source(_SRC, _OUT)
 
 
 def _load():
+    """The oracle library; NDG_ORACLE_LIB names another build of it (the
+    pin-sensitivity test loads copies with planted mistakes that way)."""
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
+        lib = ctypes.CDLL(os.environ.get("NDG_ORACLE_LIB") or build())
         lib.oracle_activate.restype = None
         lib.oracle_eval.restype = None
         lib.oracle_cull_exact.restype = None

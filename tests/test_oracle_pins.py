@@ -342,6 +342,51 @@ def test_conditioned_cull_is_sound(oracle):
         assert np.all(contrib[~keep[:, g]] < cutoff), g
 
 
+def test_conditioned_cull_interval_for_correlated_factors(oracle):
+    """Conditioned cull with strongly correlated factors, one projection and
+    one query per tile: along r (the projection's position components) a
+    query stays a candidate exactly when its distance to r . mu is within
+    3 sqrt(r^T V3 r), up to the contract's one bucket of slack on each side.
+    mu and V3 come from the textbook precision-form conditional (numpy):
+    V3 = A_pp^-1 and mu = m_p - A_pp^-1 A_pc (xc - m_c), A = (L L^T)^-1."""
+    r = np.random.default_rng(41)
+    N, G, Q, B = 4, 12, 4000, 256
+    P = N * (N + 1) // 2
+    th = np.zeros((G, P))
+    for i in range(N):
+        for j in range(i + 1):
+            idx = i * (i + 1) // 2 + j
+            th[:, idx] = np.log(r.uniform(0.05, 0.2, G)) if i == j else r.choice([-3.0, 3.0], G)
+    mix = _raw_single_rows(N, r.uniform(-0.3, 0.3, (G, N)), th, np.ones(G), np.zeros((G, 3)))
+    L, m, w = oracle.activate(raw_from(oracle, mix))
+    xc = np.array([0.1])
+    xp = r.uniform(-1.5, 1.5, size=(Q, 3))
+    x = np.concatenate([xp, np.repeat(xc[None, :], Q, axis=0)], axis=1)
+    n_in = n_out = 0
+    for trial in range(4):
+        proj = synth.projections(N, 1, 50 + trial)
+        r3 = proj[0, :3].astype(np.float64)
+        offs, ids = oracle.cull_contract(L, m, w, x, 1, proj, 0.0, 3.0, B, xc=xc)
+        keep = np.zeros((Q, G), dtype=bool)
+        for t in range(Q):
+            keep[t, ids[offs[t]:offs[t + 1]]] = True
+        v = xp @ r3
+        h = (v.max() - v.min()) / B
+        for g in range(G):
+            A = np.linalg.inv(L[g] @ L[g].T)
+            App, Apc = A[:3, :3], A[:3, 3:]
+            mu = m[g, :3] - np.linalg.solve(App, Apc @ (xc - m[g, 3:]))
+            half = 3.0 * math.sqrt(r3 @ np.linalg.solve(App, r3))
+            dist = np.abs(v - r3 @ mu)
+            inside = dist < half * (1 - 1e-5) - 1e-5
+            outside = dist > half + 2.0 * h + 1e-4
+            assert keep[inside, g].all(), (trial, g)
+            assert not keep[outside, g].any(), (trial, g)
+            n_in += int(inside.sum())
+            n_out += int(outside.sum())
+    assert n_in > 1000 and n_out > 1000
+
+
 def _raw_single_rows(N, means, thetas, alphas, gammas):
     return {"mean": np.asarray(means, np.float64).reshape(-1, N),
             "theta": np.asarray(thetas, np.float64).reshape(len(alphas), -1),
