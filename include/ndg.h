@@ -13,7 +13,9 @@
  * Conventions shared by every entry point
  *   - Every pointer is caller-owned DEVICE memory unless stated otherwise;
  *     the library never allocates or frees memory and keeps no global
- *     state.  Float arrays are FP32, row-major, contiguous, 4-byte aligned.
+ *     state, with one documented exception: ndg_forward_noalloc's static
+ *     scratch array.  Float arrays are FP32, row-major, contiguous, 4-byte
+ *     aligned.
  *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
  *     default stream).  Argument errors are detected on the host and
  *     returned before anything is launched.  Errors found on the device
