@@ -228,9 +228,11 @@ def pairs_of(cull, Qn, tile):
     return int((cnt * qt).sum().item())
 
 
-def cpu_baseline(c, ch, seconds: float = 15.0):
+def cpu_baseline(c, ch, seconds: float = 15.0, single_seconds: float = 0.0):
     """The FP64 oracle on a bounded sample of the same workload: culled
-    forward + L2 loss + gradient on a subset of tiles (host cores)."""
+    forward + L2 loss + gradient on a subset of tiles, on all host cores
+    (its OpenMP loops) and, when single_seconds > 0, on one core with a
+    sample sized to take about that long."""
     import oracle
     from paper_2405_20067_gb300 import synth  # noqa: F401  (inputs only)
     oracle.build()
@@ -260,12 +262,24 @@ def cpu_baseline(c, ch, seconds: float = 15.0):
         oracle.grad(raw, xs, TILE, so, si, gbar)
         return pairs, time.perf_counter() - t0
 
+    cores = oracle.threads()
     p1, t1 = run(4)
     n = int(min(T, max(4, 4 * seconds / max(t1, 1e-3))))
     p, t = run(n)
-    return {"value": p / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n} of {T} tiles ({p:.3g} pairs), FP64 culled forward + loss + gradient",
-            "seconds": round(t, 2)}
+    out = {"value": p / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{n} of {T} tiles ({p:.3g} pairs), FP64 culled forward + loss + gradient",
+           "seconds": round(t, 2)}
+    if single_seconds > 0:
+        n1 = int(min(T, max(1, single_seconds * n / max(t * cores, 1e-3))))
+        oracle.set_threads(1)
+        try:
+            q1, s1 = run(n1)
+        finally:
+            oracle.set_threads(cores)
+        out["single_thread"] = {"value": q1 / s1, "unit": UNIT, "cores": 1,
+                                "sample": f"{n1} of {T} tiles ({q1:.3g} pairs)",
+                                "seconds": round(s1, 2)}
+    return out
 
 
 def max_over_ranks(v: float, world: int, device="cpu") -> float:
@@ -742,7 +756,7 @@ def main():
     if not args.no_render and args.workload == "fit_n6":
         out["render"] = render_n10_1080p(device, max(3, args.steps // 4), 2, flush)
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(chosen["_c"], chosen["_ch"])
+        out["cpu_baseline"] = cpu_baseline(chosen["_c"], chosen["_ch"], single_seconds=5.0)
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -21,6 +21,7 @@ Functions and the passages they follow (paper sections / equations):
   loss_rel_l2     the relative L2 loss (Section 4.1; reading: (y - t)^2 / (y^2 + eps))
   adam            Adam update (the paper does not name its optimiser)
   densify         Section 3.3 materialisation of child Gaussians
+  threads, set_threads   host threads of the parallel loops (for timing)
 """
 from __future__ import annotations
 
@@ -76,6 +77,8 @@ def _load():
         lib.oracle_grad.restype = None
         lib.oracle_adam.restype = None
         lib.oracle_densify.restype = ctypes.c_int
+        lib.oracle_max_threads.restype = ctypes.c_int
+        lib.oracle_set_threads.restype = None
         _lib = lib
     return _lib
 
@@ -330,3 +333,13 @@ def densify(raw: Raw, G_cap: int, a_thr: float, a_child0: float, noise):
                             *[a.ctypes.data_as(_D) for a in arrs], pn,
                             flag.ctypes.data_as(_U8))
     return Raw(*arrs), Gn, flag[:G]
+
+
+def threads() -> int:
+    """Host threads the oracle's parallel loops use."""
+    return int(_load().oracle_max_threads())
+
+
+def set_threads(n: int) -> None:
+    """Sets the host threads of the oracle's parallel loops (n >= 1)."""
+    _load().oracle_set_threads(ctypes.c_int(int(n)))

@@ -28,6 +28,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OMAXN 16
 #define PIDX(i, j) ((i) * ((i) + 1) / 2 + (j))
@@ -744,4 +747,22 @@ int oracle_densify(int N, int G, int G_cap, int has_children, double a_thr,
   }
   free(fresh);
   return Gn;
+}
+
+/* Host threads the parallel loops above use (1 without OpenMP), and a way
+ * to change that count (timing of the oracle on one core and on all). */
+int oracle_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
 }

@@ -50,3 +50,15 @@ def test_clock_summary_without_samples():
     s = bench.ClockSampler(0)
     out = s.summary()
     assert out["sm_mhz"] is None and out["samples"] == 0 and out["reasons"] == []
+
+
+def test_oracle_thread_control_for_the_cpu_baseline(oracle):
+    # the baseline reports the oracle's own thread count and times one core
+    n = oracle.threads()
+    assert n >= 1
+    try:
+        oracle.set_threads(1)
+        assert oracle.threads() == 1
+    finally:
+        oracle.set_threads(n)
+    assert oracle.threads() == n
