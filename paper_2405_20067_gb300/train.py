@@ -209,7 +209,9 @@ class Trainer:
     def check(self):
         """Synchronises: applies a pending row count, verifies the device
         status word and the candidate capacity (rebuilding larger buffers
-        when it overflowed)."""
+        when it overflowed).  Steps taken since the overflow used truncated
+        candidate lists: their outputs and gradients miss the dropped pairs
+        (Adam has applied them); a captured graph has to be captured again."""
         st = ndg.read_status(self.ev.ws)
         Gn = int(self.G_new.item())
         if self.mix.has_children and Gn >= self.mix.G:
