@@ -93,10 +93,10 @@ def _tr(trace):
     return ctypes.byref(trace.c) if trace is not None else None
 
 
-EXPORTS = ["ndg_workspace_size", "ndg_build_cull", "ndg_build_cull_conditioned", "ndg_forward", "ndg_loss_l2", "ndg_loss_rel_l2",
-           "ndg_backward",
-           "ndg_adam", "ndg_densify", "ndg_read_status", "ndg_status_string", "ndg_version",
-           "ndg_forward_noalloc", "ndg_selftest_timeout"]
+EXPORTS = ["ndg_workspace_size", "ndg_build_cull", "ndg_build_cull_conditioned", "ndg_forward",
+           "ndg_loss_l2", "ndg_loss_rel_l2", "ndg_backward", "ndg_adam", "ndg_densify",
+           "ndg_read_status", "ndg_status_string", "ndg_version", "ndg_forward_noalloc",
+           "ndg_selftest_timeout"]
 NDG_ERR_SCRATCH_LIMIT = 7
 
 
@@ -130,10 +130,9 @@ def lib():
         L.ndg_status_string.argtypes = [ctypes.c_int]
         L.ndg_status_string.restype = ctypes.c_char_p
         L.ndg_version.restype = ctypes.c_int
-        for name in ["ndg_build_cull", "ndg_build_cull_conditioned", "ndg_forward", "ndg_loss_l2", "ndg_loss_rel_l2",
-                     "ndg_backward", "ndg_adam",
-                     "ndg_densify", "ndg_read_status", "ndg_forward_noalloc",
-                     "ndg_selftest_timeout"]:
+        for name in ["ndg_build_cull", "ndg_build_cull_conditioned", "ndg_forward", "ndg_loss_l2",
+                     "ndg_loss_rel_l2", "ndg_backward", "ndg_adam", "ndg_densify",
+                     "ndg_read_status", "ndg_forward_noalloc", "ndg_selftest_timeout"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
