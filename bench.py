@@ -688,6 +688,10 @@ def main():
             print(json.dumps({"render_batch": run_render_batch(device)}))
         return
     peaks, peak_kind = load_peaks()
+    from paper_2405_20067_gb300 import ndg as _ndg
+    # measured pipe rates of this GPU (ndg_probe_pipe): the MUFU exponential
+    # (one per pair in every evaluation kernel) and the FP32 FMA
+    probe = {"ex2": _ndg.probe_pipe(0), "ffma": _ndg.probe_pipe(1)}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)  # > 129 MB L2
     chosen = run_fit("tc", args.steps, args.warmup, device, flush, world,
                      max(3, args.steps // 2), bwd_form=args.bwd_form, graph=not args.no_graph)
@@ -718,7 +722,16 @@ def main():
                     "executed_frac": round(executed / tc_peak, 4),
                     "executed_note": f"{exe_bwd} MMA flop/pair issued: FP16 hi/lo split (3 "
                                      "products) and the colour-blocked Psi operand",
-                    "mufu_ex2_per_s": mean_pairs / t_bwd}
+                    "tensor_frac": round(achieved / tc_peak, 4)}
+        mufu_frac = mean_pairs / t_bwd / probe["ex2"]["per_s"]
+        roofline["mufu"] = {"achieved": mean_pairs / t_bwd, "peak": probe["ex2"]["per_s"],
+                            "unit": "ex2/s", "frac": round(mufu_frac, 4),
+                            "per_clk_per_sm": round(probe["ex2"]["per_clk_per_sm"], 2),
+                            "algorithmic": "1 ex2 per pair",
+                            "peak_source": "ndg_probe_pipe(0) in this run (MUFU ex2.approx, "
+                                           "all SMs, best of 5)"}
+        roofline["binding"] = "mufu" if mufu_frac > roofline["tensor_frac"] else "tensor"
+        roofline["binding_frac"] = round(max(mufu_frac, roofline["tensor_frac"]), 4)
     else:
         achieved = mean_pairs * bwd_f / t_bwd / 1e12
         roofline = {"bound": "alu", "kernel": f"bwd_kernel<{N_DIM}> (per-pair partials, FP32 pipe)",
@@ -733,6 +746,8 @@ def main():
     kernels["forward"]["tc_alg_tflops"] = round(mean_pairs * alg_fwd / t_fwd / 1e12, 3)
     kernels["forward"]["tc_executed_tflops"] = round(mean_pairs * exe_fwd / t_fwd / 1e12, 2)
     kernels["forward"]["fp32_equiv_tflops"] = round(mean_pairs * fwd_f / t_fwd / 1e12, 3)
+    kernels["forward"]["tensor_frac"] = round(mean_pairs * alg_fwd / t_fwd / 1e12 / tc_peak, 4)
+    kernels["forward"]["mufu_frac"] = round(mean_pairs / t_fwd / probe["ex2"]["per_s"], 4)
     if rank != 0:
         return
     out = {"metric": METRIC, "value": chosen["value"], "unit": UNIT, "n_gpus": world,
@@ -748,7 +763,9 @@ def main():
                       "l2": "256 MB buffer written between timed steps (untimed)",
                       "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
            "roofline": roofline, "kernels_ms": kernels, "gpu_launches": chosen["gpu_launches"],
-           "e2e": chosen["e2e"], "clocks": chosen["clocks"]}
+           "e2e": chosen["e2e"], "clocks": chosen["clocks"],
+           "pipe_probe": {k: {"per_clk_per_sm": round(v["per_clk_per_sm"], 2),
+                              "per_s": v["per_s"]} for k, v in probe.items()}}
     if plain is not None:
         out["fp32_form"] = {"value": plain["value"], "ms_per_step": plain["ms_per_step"],
                             "forward_ms": round(plain["kernels_ms"]["forward"], 4),

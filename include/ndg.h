@@ -58,7 +58,8 @@ typedef enum {
   NDG_ERR_INVALID_ARG = 1, /* bad size, NULL or misaligned pointer       */
   NDG_ERR_CAPACITY = 2,    /* candidate entries exceeded E_cap           */
   NDG_ERR_CUDA = 3,        /* a CUDA launch or copy failed               */
-  NDG_ERR_NUMERIC = 4,     /* non-finite value in the parameters         */
+  NDG_ERR_NUMERIC = 4,     /* non-finite activated value (L, m or w) of an
+                              evaluated Gaussian                          */
   NDG_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out         */
   NDG_ERR_WORKSPACE = 6,   /* ws smaller than ndg_workspace_size()       */
   NDG_ERR_SCRATCH_LIMIT = 7 /* input larger than ndg_forward_noalloc's
@@ -252,18 +253,23 @@ ndg_status ndg_densify(ndg_mixture* mix, float a_thr, float a_child0,
  * the device synchronisation an allocation may cause).  The paper has no
  * counterpart; it is a deployment convenience.  Same result as ndg_forward
  * (mode NDG_MODE_FP32) on the same inputs; the caller still owns mix, q,
- * cull and y.  Its scratch (the prepared records, Ge * R * 4 bytes with
- * Ge = G (1 + has_children) and R = N(N+1)/2 + N + 3 rounded up to a
- * multiple of 4) lives in one static device array of
+ * cull and y.  Argument errors (sizes, NULL or misaligned pointers) are the
+ * same as ndg_forward's and return NDG_ERR_INVALID_ARG before anything runs;
+ * cull->E_dev is not read.  Its scratch (the prepared records, Ge * R * 4
+ * bytes with Ge = G (1 + has_children) and R = N(N+1)/2 + N + 3 rounded up
+ * to a multiple of 4) lives in one static device array of
  * NDG_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
  * exit; larger mixtures return NDG_ERR_SCRATCH_LIMIT before anything runs
  * (N = 6: up to 131072 evaluated Gaussians; N = 10: up to 61680).  The
  * first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race
- * and must be serialised by the caller.  Device-side status (non-finite
- * parameters) is not reported by this variant.  Calls nothing that
- * allocates. */
+ * (cudaGetSymbolAddress) and keeps it for the life of the process, so make
+ * that first call before any stream capture, and do not call this entry
+ * point on a device after cudaDeviceReset.  All calls share the array:
+ * calls that overlap on the GPU race and must be serialised by the caller.
+ * NDG_ERR_CUDA reports a launch failure of this call only (an error left
+ * pending by an earlier call is neither reported nor cleared).  Device-side
+ * status (non-finite parameters) is not reported by this variant.  Calls
+ * nothing that allocates. */
 #define NDG_NOALLOC_SCRATCH_BYTES (16 << 20)
 ndg_status ndg_forward_noalloc(const ndg_mixture* mix, const ndg_queries* q,
                                const ndg_cull* cull, float* y, ndg_stream stream);
@@ -277,6 +283,19 @@ ndg_status ndg_forward_noalloc(const ndg_mixture* mix, const ndg_queries* q,
  * faults and the context stays usable.  ws: any workspace (only its status
  * word is used). */
 ndg_status ndg_selftest_timeout(int which, void* ws, size_t ws_bytes, ndg_stream stream);
+
+/* Measurement helper (no counterpart in the paper): throughput probe of one
+ * arithmetic pipe, for the rooflines the benchmark reports.  which = 0: the
+ * MUFU exponential (ex2.approx, one per Gaussian-query pair in every
+ * evaluation kernel); which = 1: the FP32 FMA.  Launches `blocks` blocks of
+ * `threads` threads (a multiple of 32, at most 1024), at most one block per
+ * SM at a time; every thread executes 8 x iters dependent instructions in 8
+ * independent chains.  cycles_dev [blocks] receives each block's clock64
+ * cycles around its loop, sink_dev [blocks * threads] the chains' results
+ * (so nothing is optimised away).  Rate per SM per clock = threads * 8 *
+ * iters / cycles. */
+ndg_status ndg_probe_pipe(int which, int blocks, int threads, int iters, long long* cycles_dev,
+                          float* sink_dev, ndg_stream stream);
 
 /* Synchronises `stream`, copies the workspace status word to *device_status
  * (an ndg_status value) and clears it. */

@@ -24,6 +24,50 @@
 
 using namespace ndg;
 
+namespace ndg {
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+ndg_status check_mix(const ndg_mixture* m) {
+  if (!m) return NDG_ERR_INVALID_ARG;
+  if (m->N < 1 || m->N > NDG_MAX_N || m->G < 0 || m->G_cap < m->G) return NDG_ERR_INVALID_ARG;
+  if (m->G > (1 << 30)) return NDG_ERR_INVALID_ARG;
+  if (m->G > 0) {
+    const float* need[4] = {m->mean, m->theta, m->alpha_raw, m->color_raw};
+    for (const float* p : need)
+      if (!p || !aligned(p, 4)) return NDG_ERR_INVALID_ARG;
+    if (m->has_children) {
+      const float* ch[4] = {m->u_theta, m->m_u, m->c_alpha_raw, m->c_color_raw};
+      for (const float* p : ch)
+        if (!p || !aligned(p, 4)) return NDG_ERR_INVALID_ARG;
+    }
+  }
+  return NDG_OK;
+}
+
+ndg_status check_queries(const ndg_queries* q) {
+  if (!q || q->Q < 0 || q->tile_size < 1 || q->tile_size > NDG_MAX_TILE) return NDG_ERR_INVALID_ARG;
+  if (q->Q > 0 && (!q->x || !aligned(q->x, 4))) return NDG_ERR_INVALID_ARG;
+  return NDG_OK;
+}
+
+ndg_status check_cull_params(const ndg_cull_params* cp) {
+  if (!cp || cp->k < 0 || cp->k > NDG_MAX_K) return NDG_ERR_INVALID_ARG;
+  if (cp->k > 0 && !cp->proj) return NDG_ERR_INVALID_ARG;
+  if (cp->buckets < 1 || cp->buckets > NDG_MAX_BUCKETS) return NDG_ERR_INVALID_ARG;
+  if (!(cp->cutoff >= 0.0f) || !std::isfinite(cp->cutoff)) return NDG_ERR_INVALID_ARG;
+  if (!(cp->cutoff > 0.0f) && !(cp->k_sigma >= 0.0f)) return NDG_ERR_INVALID_ARG;
+  return NDG_OK;
+}
+
+ndg_status check_cull(const ndg_cull* c) {
+  if (!c || !c->offsets || !c->E_dev || c->E_cap < 0) return NDG_ERR_INVALID_ARG;
+  if (c->E_cap > 0 && !c->ids) return NDG_ERR_INVALID_ARG;
+  return NDG_OK;
+}
+
+}  // namespace ndg
+
 namespace {
 
 constexpr size_t kAlign = 256;
@@ -120,46 +164,6 @@ BwdLayout bwd_layout(const Sizes& z, size_t base) {
   }
   b.end = r.off;
   return b;
-}
-
-bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
-
-ndg_status check_mix(const ndg_mixture* m) {
-  if (!m) return NDG_ERR_INVALID_ARG;
-  if (m->N < 1 || m->N > NDG_MAX_N || m->G < 0 || m->G_cap < m->G) return NDG_ERR_INVALID_ARG;
-  if (m->G > (1 << 30)) return NDG_ERR_INVALID_ARG;
-  if (m->G > 0) {
-    const float* need[4] = {m->mean, m->theta, m->alpha_raw, m->color_raw};
-    for (const float* p : need)
-      if (!p || !aligned(p, 4)) return NDG_ERR_INVALID_ARG;
-    if (m->has_children) {
-      const float* ch[4] = {m->u_theta, m->m_u, m->c_alpha_raw, m->c_color_raw};
-      for (const float* p : ch)
-        if (!p || !aligned(p, 4)) return NDG_ERR_INVALID_ARG;
-    }
-  }
-  return NDG_OK;
-}
-
-ndg_status check_queries(const ndg_queries* q) {
-  if (!q || q->Q < 0 || q->tile_size < 1 || q->tile_size > NDG_MAX_TILE) return NDG_ERR_INVALID_ARG;
-  if (q->Q > 0 && (!q->x || !aligned(q->x, 4))) return NDG_ERR_INVALID_ARG;
-  return NDG_OK;
-}
-
-ndg_status check_cull_params(const ndg_cull_params* cp) {
-  if (!cp || cp->k < 0 || cp->k > NDG_MAX_K) return NDG_ERR_INVALID_ARG;
-  if (cp->k > 0 && !cp->proj) return NDG_ERR_INVALID_ARG;
-  if (cp->buckets < 1 || cp->buckets > NDG_MAX_BUCKETS) return NDG_ERR_INVALID_ARG;
-  if (!(cp->cutoff >= 0.0f) || !std::isfinite(cp->cutoff)) return NDG_ERR_INVALID_ARG;
-  if (!(cp->cutoff > 0.0f) && !(cp->k_sigma >= 0.0f)) return NDG_ERR_INVALID_ARG;
-  return NDG_OK;
-}
-
-ndg_status check_cull(const ndg_cull* c) {
-  if (!c || !c->offsets || !c->E_dev || c->E_cap < 0) return NDG_ERR_INVALID_ARG;
-  if (c->E_cap > 0 && !c->ids) return NDG_ERR_INVALID_ARG;
-  return NDG_OK;
 }
 
 Sizes make_sizes(const ndg_mixture* m, const ndg_queries* q, const ndg_cull_params* cp,
@@ -619,6 +623,16 @@ ndg_status ndg_densify(ndg_mixture* mix, float a_thr, float a_child0, const floa
   tr.begin();
   tr += launch_densify(mix->N, a, (cudaStream_t)stream);
   tr.end();
+  return cuda_ok();
+}
+
+ndg_status ndg_probe_pipe(int which, int blocks, int threads, int iters, long long* cycles_dev,
+                          float* sink_dev, ndg_stream stream) {
+  if ((which != 0 && which != 1) || blocks < 1 || blocks > (1 << 20) || threads < 32 ||
+      threads > 1024 || threads % 32 != 0 || iters < 1 || !cycles_dev || !sink_dev ||
+      !aligned(cycles_dev, 8) || !aligned(sink_dev, 4))
+    return NDG_ERR_INVALID_ARG;
+  launch_probe_pipe(which, blocks, threads, iters, cycles_dev, sink_dev, (cudaStream_t)stream);
   return cuda_ok();
 }
 

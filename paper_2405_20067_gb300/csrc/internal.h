@@ -5,7 +5,18 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "ndg.h"
+
 namespace ndg {
+
+// ---- host-side argument checks (api.cu), shared by every entry point ------
+// Each returns NDG_OK or NDG_ERR_INVALID_ARG without touching the device:
+// sizes in range, required pointers present and 4-byte aligned (FP32 data).
+bool aligned(const void* p, size_t a);
+ndg_status check_mix(const ndg_mixture* m);
+ndg_status check_queries(const ndg_queries* q);
+ndg_status check_cull_params(const ndg_cull_params* cp);
+ndg_status check_cull(const ndg_cull* c);  // also requires E_dev
 
 // ---- primitives (primitives.cu) ------------------------------------------
 // Exclusive prefix sum of n int64 values: out[0..n], out[n] = total.

@@ -135,5 +135,7 @@ int launch_segsum(const float* part, int RP, const long long* goff, int Ge, cons
 int launch_chain(int N, const ChainArgs& a, cudaStream_t s);
 int launch_adam(const AdamArgs& a, cudaStream_t s);
 int launch_densify(int N, const DensifyArgs& a, cudaStream_t s);
+int launch_probe_pipe(int which, int blocks, int threads, int iters, long long* cycles,
+                      float* sink, cudaStream_t s);
 
 }  // namespace ndg

@@ -35,7 +35,9 @@ void* g_scratch_addr[kMaxDevices] = {};
 // Device address of the scratch array on the current device.  Host code
 // cannot use g_noalloc_scratch directly: on the host that name is only a
 // stand-in.  The address is looked up once per device, the first time this
-// entry point runs on it.
+// entry point runs on it, and kept for the life of the process; a
+// cudaDeviceReset reloads the module and invalidates it (callers that reset a
+// device must not call this entry point on it afterwards).
 ndg_status scratch_address(void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return NDG_ERR_CUDA;
@@ -54,22 +56,19 @@ ndg_status scratch_address(void** out) {
 extern "C" ndg_status ndg_forward_noalloc(const ndg_mixture* mix, const ndg_queries* q,
                                           const ndg_cull* cull, float* y, ndg_stream stream) {
   using namespace ndg;
-  if (!mix || mix->N < 1 || mix->N > NDG_MAX_N || mix->G < 0 || mix->G_cap < mix->G)
-    return NDG_ERR_INVALID_ARG;
-  if (mix->G > 0 && (!mix->mean || !mix->theta || !mix->alpha_raw || !mix->color_raw))
-    return NDG_ERR_INVALID_ARG;
-  if (mix->G > 0 && mix->has_children &&
-      (!mix->u_theta || !mix->m_u || !mix->c_alpha_raw || !mix->c_color_raw))
-    return NDG_ERR_INVALID_ARG;
-  if (!q || q->Q < 0 || q->tile_size < 1 || q->tile_size > NDG_MAX_TILE) return NDG_ERR_INVALID_ARG;
-  if (q->Q > 0 && (!q->x || !y)) return NDG_ERR_INVALID_ARG;
-  if (!cull || !cull->offsets || cull->E_cap < 0 || (cull->E_cap > 0 && !cull->ids))
+  // the same argument rules as ndg_forward (sizes, NULL and misaligned
+  // pointers), except that the candidate count E_dev is not needed here
+  ndg_status st;
+  if ((st = check_mix(mix)) || (st = check_queries(q))) return st;
+  if (q->Q > 0 && (!y || !aligned(y, 4))) return NDG_ERR_INVALID_ARG;
+  if (!cull || !cull->offsets || !aligned(cull->offsets, 8) || cull->E_cap < 0 ||
+      (cull->E_cap > 0 && (!cull->ids || !aligned(cull->ids, 4))))
     return NDG_ERR_INVALID_ARG;
   const long long Ge = (long long)mix->G * (mix->has_children ? 2 : 1);
   const size_t need = (size_t)Ge * rec_floats(mix->N) * sizeof(float);
   if (need > (size_t)NDG_NOALLOC_SCRATCH_BYTES) return NDG_ERR_SCRATCH_LIMIT;
   void* scratch = nullptr;
-  ndg_status st = scratch_address(&scratch);
+  st = scratch_address(&scratch);
   if (st != NDG_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   PrepArgs pa{};
@@ -85,7 +84,6 @@ extern "C" ndg_status ndg_forward_noalloc(const ndg_mixture* mix, const ndg_quer
   pa.c_color_raw = mix->c_color_raw;
   pa.rec = (float*)scratch;
   pa.status = nullptr;
-  launch_prep(mix->N, pa, s);
   FwdArgs fa{};
   fa.x = q->x;
   fa.Q = q->Q;
@@ -95,6 +93,16 @@ extern "C" ndg_status ndg_forward_noalloc(const ndg_mixture* mix, const ndg_quer
   fa.rec = pa.rec;
   fa.Ge = pa.Ge;
   fa.y = y;
+  // A launch failure of this call is an error that was not pending before
+  // it.  An error left pending by an earlier, unrelated call is neither
+  // reported as this call's nor cleared.
+  const cudaError_t before = cudaPeekAtLastError();
+  launch_prep(mix->N, pa, s);
   launch_fwd(mix->N, fa, (q->Q + q->tile_size - 1) / q->tile_size, s);
-  return cudaGetLastError() == cudaSuccess ? NDG_OK : NDG_ERR_CUDA;
+  const cudaError_t after = cudaPeekAtLastError();
+  if (after != cudaSuccess && after != before) {
+    (void)cudaGetLastError();  // this call's own launch error: reported here
+    return NDG_ERR_CUDA;
+  }
+  return NDG_OK;
 }

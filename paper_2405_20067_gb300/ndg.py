@@ -22,7 +22,12 @@ LIB_PATH = os.path.join(_HERE, "_build", "libndg.so")
 _lib = None
 
 NDG_OK = 0
+NDG_ERR_INVALID_ARG = 1
 NDG_ERR_CAPACITY = 2
+NDG_ERR_CUDA = 3
+NDG_ERR_NUMERIC = 4
+NDG_ERR_TIMEOUT = 5
+NDG_ERR_WORKSPACE = 6
 NDG_MODE_FP32 = 0
 NDG_MODE_TC = 1
 NDG_MODE_AUTO = 2  # forward: tensor cores on tiles with >= auto_min_candidates(N) candidates
@@ -96,7 +101,7 @@ def _tr(trace):
 EXPORTS = ["ndg_workspace_size", "ndg_build_cull", "ndg_build_cull_conditioned", "ndg_forward",
            "ndg_loss_l2", "ndg_loss_rel_l2", "ndg_backward", "ndg_adam", "ndg_densify",
            "ndg_read_status", "ndg_status_string", "ndg_version", "ndg_forward_noalloc",
-           "ndg_selftest_timeout"]
+           "ndg_selftest_timeout", "ndg_probe_pipe"]
 NDG_ERR_SCRATCH_LIMIT = 7
 
 
@@ -126,13 +131,16 @@ def lib():
         L.ndg_densify.argtypes = [M, ctypes.c_float, ctypes.c_float, _P, M, M, _P, _P, sz, _P, TR]
         L.ndg_forward_noalloc.argtypes = [M, Qp, C, _P, _P]
         L.ndg_selftest_timeout.argtypes = [ctypes.c_int, _P, sz, _P]
+        L.ndg_probe_pipe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
+                                     _P, _P]
         L.ndg_read_status.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_int)]
         L.ndg_status_string.argtypes = [ctypes.c_int]
         L.ndg_status_string.restype = ctypes.c_char_p
         L.ndg_version.restype = ctypes.c_int
         for name in ["ndg_build_cull", "ndg_build_cull_conditioned", "ndg_forward", "ndg_loss_l2",
                      "ndg_loss_rel_l2", "ndg_backward", "ndg_adam", "ndg_densify",
-                     "ndg_read_status", "ndg_forward_noalloc", "ndg_selftest_timeout"]:
+                     "ndg_read_status", "ndg_forward_noalloc", "ndg_selftest_timeout",
+                     "ndg_probe_pipe"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -328,6 +336,34 @@ def selftest_timeout(which: int, ws: torch.Tensor, stream=None):
     records NDG_ERR_TIMEOUT in the workspace status word (read_status)."""
     _check(lib().ndg_selftest_timeout(int(which), _ptr(ws), ws.numel(), _stream(stream)),
            "ndg_selftest_timeout")
+
+
+def probe_pipe(which: int, reps: int = 5, iters: int = 2048, threads: int = 1024) -> dict:
+    """Throughput of one arithmetic pipe (0: MUFU ex2, 1: FP32 FMA) through
+    ndg_probe_pipe: the best of `reps` launches of one block per SM.  Returns
+    the rate per SM per clock (from the blocks' clock64 cycles) and per
+    second (from CUDA events around the launch)."""
+    dev = torch.cuda.current_device()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = sms
+    cycles = torch.zeros(blocks, dtype=torch.int64, device="cuda")
+    sink = torch.zeros(blocks * threads, dtype=torch.float32, device="cuda")
+    ops = blocks * threads * 8 * iters
+    best = None
+    for _ in range(reps + 1):  # the first launch warms up
+        b, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b.record()
+        _check(lib().ndg_probe_pipe(int(which), blocks, threads, iters, _ptr(cycles), _ptr(sink),
+                                    _stream()), "ndg_probe_pipe")
+        e.record()
+        torch.cuda.synchronize()
+        ms = b.elapsed_time(e)
+        cyc = float(cycles.float().median().item())
+        r = {"per_clk_per_sm": threads * 8 * iters / cyc, "per_s": ops / (ms * 1e-3),
+             "ms": ms, "cycles": cyc, "sms": sms}
+        if best is None or r["per_s"] > best["per_s"]:
+            best = r
+    return best
 
 
 def loss_rel_l2(y: torch.Tensor, target: torch.Tensor, dy: torch.Tensor, loss: torch.Tensor,

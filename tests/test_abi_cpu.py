@@ -107,3 +107,45 @@ def test_mode_constants_match_header(ndg):
     lim, lo, hi = (int(v) for v in m.groups())
     for N in range(1, 13):
         assert ndg.auto_min_candidates(N) == (lo if N <= lim else hi), N
+
+
+def test_noalloc_rejects_bad_pointers_on_host(ndg):
+    """ndg_forward_noalloc applies ndg_forward's argument rules (NULL and
+    misaligned FP32 pointers, sizes) before any CUDA call, so a bad pointer
+    is an error status, never a launch."""
+    L = ndg.lib()
+    q = ndg.QueriesC(100, 256, ctypes.c_void_p(0x2000))
+    cull = ndg.CullC(ctypes.c_void_p(0x4000), ctypes.c_void_p(0x5000), 100, None)
+    y = ctypes.c_void_p(0x7000)
+    fake = ctypes.c_void_p(0x1000)
+    odd = ctypes.c_void_p(0x1002)  # not 4-byte aligned
+    for i in range(4):  # each parent parameter misaligned in turn
+        ptrs = [fake] * 4
+        ptrs[i] = odd
+        m = ndg.MixtureC(6, 10, 10, 0, *ptrs, None, None, None, None)
+        assert L.ndg_forward_noalloc(ctypes.byref(m), ctypes.byref(q), ctypes.byref(cull), y,
+                                     None) == 1, i
+    for i in range(4):  # each child parameter misaligned in turn
+        ch = [fake] * 4
+        ch[i] = odd
+        m = ndg.MixtureC(6, 10, 10, 1, fake, fake, fake, fake, *ch)
+        assert L.ndg_forward_noalloc(ctypes.byref(m), ctypes.byref(q), ctypes.byref(cull), y,
+                                     None) == 1, i
+    m = _mix_c(ndg)
+    bad_q = ndg.QueriesC(100, 256, ctypes.c_void_p(0x2001))
+    assert L.ndg_forward_noalloc(ctypes.byref(m), ctypes.byref(bad_q), ctypes.byref(cull), y,
+                                 None) == 1
+    assert L.ndg_forward_noalloc(ctypes.byref(m), ctypes.byref(q), ctypes.byref(cull),
+                                 ctypes.c_void_p(0x7002), None) == 1  # y misaligned
+    bad_cull = ndg.CullC(ctypes.c_void_p(0x4004), ctypes.c_void_p(0x5000), 100, None)
+    assert L.ndg_forward_noalloc(ctypes.byref(m), ctypes.byref(q), ctypes.byref(bad_cull), y,
+                                 None) == 1  # int64 offsets misaligned
+    bad_ids = ndg.CullC(ctypes.c_void_p(0x4000), ctypes.c_void_p(0x5002), 100, None)
+    assert L.ndg_forward_noalloc(ctypes.byref(m), ctypes.byref(q), ctypes.byref(bad_ids), y,
+                                 None) == 1
+    assert L.ndg_forward_noalloc(ctypes.byref(_mix_c(ndg, N=13)), ctypes.byref(q),
+                                 ctypes.byref(cull), y, None) == 1
+    # beyond the fixed scratch: refused before any launch as well
+    big = ndg.MixtureC(6, 200_000, 200_000, 0, fake, fake, fake, fake, None, None, None, None)
+    assert L.ndg_forward_noalloc(ctypes.byref(big), ctypes.byref(q), ctypes.byref(cull), y,
+                                 None) == ndg.NDG_ERR_SCRATCH_LIMIT

@@ -444,3 +444,66 @@ def test_config0_l2_loss_and_gradient(ndg, oracle):
     got = {n: getattr(grad, n)[:1000].cpu().numpy() for n in NAMES[:4]}
     rep = assert_grads_close(got, want, NAMES[:4])
     print("config 0: loss %.6e; " % loss.item() + " ".join(f"{n}={v:.1e}" for n, v in rep.items()))
+
+
+@pytest.mark.parametrize("mode", ["fp32", "tc"])
+def test_backward_above_32768_tiles_matches_oracle(ndg, oracle, mode):
+    """More than 32768 tiles: the backward orders the entries Gaussian-major by
+    a radix sort of the ids (the counting sort covers up to 32768 tiles).
+    Tiles of 16 queries over 540,000 queries (33,750 tiles); gradients
+    against the oracle (FP32 form 1e-4, tensor-core form 1e-3 per tensor) and
+    a second backward bit-identical."""
+    import torch
+    N, G, Q, tile, k = 6, 1000, 540_000, 16, 16
+    seed = 910
+    mix, ch, x = make_case(N, G, Q, seed, children=True)
+    gm, xt, proj, cp, ev, E = gpu_setup(ndg, N, mix, ch, x, tile, k, 1 / 255, 3.0, 64, seed)
+    assert ev.T > 32768
+    dy = (synth.rng(seed + 9).standard_normal((Q, 3)) / (3 * Q)).astype(np.float32)
+    md = ndg.NDG_MODE_TC if mode == "tc" else ndg.NDG_MODE_FP32
+    dyt = torch.as_tensor(dy).cuda()
+    grad = ev.backward(gm, dyt, mode=md)
+    assert ndg.read_status(ev.ws) == 0
+    raw = oracle_raw(oracle, mix, ch)
+    L, m, w = oracle.activate(raw)
+    o_offs, o_ids = oracle.cull_contract(L, m, w, x.astype(np.float64), tile, proj, 1 / 255, 3.0, 64)
+    assert E == o_offs[-1]
+    want = oracle.grad(raw, x.astype(np.float64), tile, o_offs, o_ids, dy.astype(np.float64))
+    got = {n: getattr(grad, n)[:G].cpu().numpy() for n in NAMES}
+    rep = assert_grads_close(got, want, NAMES, rtol=1e-3 if mode == "tc" else 1e-4)
+    print(f"{mode} T={ev.T} E={E}: " + " ".join(f"{n}={v:.1e}" for n, v in rep.items()))
+    grad2 = ev.backward(gm, dyt, mode=md)
+    for n in NAMES:
+        assert torch.equal(getattr(grad, n), getattr(grad2, n)), n
+
+
+def test_non_finite_parameter_sets_numeric_status(ndg):
+    """A raw parameter whose activation is not finite (NaN, or +inf
+    brightness; planted on the host) makes the preparation report
+    NDG_ERR_NUMERIC in the workspace status word; nothing faults, and the
+    next call with finite parameters reports NDG_OK."""
+    import torch
+    N, G, Q, tile, k = 6, 500, 4096, 256, 8
+    seed = 920
+    mix, ch, x = make_case(N, G, Q, seed, children=True)
+    gm, xt, proj, cp, ev, E = gpu_setup(ndg, N, mix, ch, x, tile, k, 1 / 255, 3.0, 64, seed)
+    assert ndg.read_status(ev.ws) == 0
+    for field, value in (("theta", float("nan")), ("alpha_raw", float("inf")),
+                         ("m_u", float("nan")), ("c_color_raw", float("nan"))):
+        t = getattr(gm, field)
+        keep = t.clone()
+        t.view(-1)[7] = value
+        ev.forward(gm, mode=ndg.NDG_MODE_TC)
+        assert ndg.read_status(ev.ws) == ndg.NDG_ERR_NUMERIC, field
+        assert ndg.read_status(ev.ws) == 0  # reading clears the word
+        ndg.build_cull(gm, xt, tile, cp, ev.cull, ev.ws)
+        assert ndg.read_status(ev.ws) == ndg.NDG_ERR_NUMERIC, field
+        t.copy_(keep)
+        ev.build(gm)
+        ev.forward(gm, mode=ndg.NDG_MODE_TC)
+        ev.backward(gm, torch.ones(Q, 3, device="cuda") / Q, mode=ndg.NDG_MODE_TC)
+        assert ndg.read_status(ev.ws) == 0, field
+    # a raw colour of -inf activates to the finite colour 0: not an error
+    gm.c_color_raw.view(-1)[7] = float("-inf")
+    ev.forward(gm, mode=ndg.NDG_MODE_TC)
+    assert ndg.read_status(ev.ws) == 0
