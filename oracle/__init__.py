@@ -175,8 +175,11 @@ def eval(L, m, w, x, tile=256, offsets=None, ids=None):
     return y
 
 
-def cull_exact(L, m, w, x, tile, proj, cutoff, k_sigma):
-    """keep [T, Ge] uint8 from the real-valued FP64 test (Eq. 3-5)."""
+def cull_exact(L, m, w, x, tile, proj, cutoff, k_sigma, n_parents=None, child_k_min=0.0):
+    """keep [T, Ge] uint8 from the real-valued FP64 test (Eq. 3-5).
+    n_parents: evaluated Gaussians at or above this index are children, whose
+    radius is at least child_k_min (> 0; reading R7, Section 3.3); None: no
+    children."""
     lib = _load()
     L, pL = _d(L)
     m, pm = _d(m)
@@ -189,18 +192,21 @@ def cull_exact(L, m, w, x, tile, proj, cutoff, k_sigma):
     keep = np.zeros((T, Ge), dtype=np.uint8)
     lib.oracle_cull_exact(N, Ge, pL, pm, pw, ctypes.c_longlong(Q), px, tile,
                           proj.shape[0], pp, ctypes.c_double(cutoff),
-                          ctypes.c_double(k_sigma), keep.ctypes.data_as(_U8))
+                          ctypes.c_double(k_sigma), Ge if n_parents is None else int(n_parents),
+                          ctypes.c_double(child_k_min), keep.ctypes.data_as(_U8))
     return keep
 
 
-def cull_contract(L, m, w, x, tile, proj, cutoff, k_sigma, buckets, tiles=None, xc=None):
+def cull_contract(L, m, w, x, tile, proj, cutoff, k_sigma, buckets, tiles=None, xc=None,
+                  n_parents=None, child_k_min=0.0):
     """(offsets, ids [E] int32) from the FP32 bucket contract.
 
     tiles=None: every tile, offsets [T+1] int64.  Otherwise the lists of the
     given tile indices only (in that order), offsets [len(tiles)+1]; each list
     equals that tile's list in the full run (the ranges and keys still come
     from the whole query set).  xc (N - 3 values): the contract on position
-    for the Gaussians restricted to the constant inputs xc (condition())."""
+    for the Gaussians restricted to the constant inputs xc (condition()).
+    n_parents, child_k_min: children's radius floor, as in cull_exact."""
     lib = _load()
     L, pL = _d(L)
     m, pm = _d(m)
@@ -224,6 +230,7 @@ def cull_contract(L, m, w, x, tile, proj, cutoff, k_sigma, buckets, tiles=None, 
         pxc = None
     args = (N, Ge, pL, pm, pw, ctypes.c_longlong(Q), px, tile, k, pp,
             ctypes.c_double(cutoff), ctypes.c_double(k_sigma), buckets,
+            Ge if n_parents is None else int(n_parents), ctypes.c_double(child_k_min),
             ctypes.c_longlong(n_sel), psel, pxc)
     E = lib.oracle_cull_contract(*args, offsets.ctypes.data_as(_LL), None)
     ids = np.zeros(max(E, 1), dtype=np.int32)

@@ -140,13 +140,28 @@ void oracle_eval(int N, int Ge, const double* L, const double* m,
  * contribution cutoff > 0 the radius is the one beyond which
  * w_max exp(-s/2) < cutoff, i.e. sqrt(2 ln(w_max / cutoff)); a Gaussian
  * whose largest weight is below the cutoff is culled everywhere (-1). */
-static double cull_radius(const double* w, double cutoff, double k_sigma) {
+static double cutoff_radius(const double* w, double cutoff, double k_sigma) {
   if (!(cutoff > 0.0)) return k_sigma;
   double wm = w[0];
   if (w[1] > wm) wm = w[1];
   if (w[2] > wm) wm = w[2];
   if (!(wm > cutoff)) return -1.0;
   return sqrt(2.0 * log(wm / cutoff));
+}
+
+/* The radius of evaluated Gaussian g.  Section 3.3: a child starts with a
+ * negligible, randomised contribution spanning its parent and is optimised
+ * with the mixture until it materialises.  Reading R7: a child (g >=
+ * n_parents) keeps a radius of at least child_k_min (> 0, e.g. the 3 of
+ * Eq. 5) even when its largest weight is below the cutoff, so it is still
+ * evaluated, and receives a gradient, where it spans its parent; a larger
+ * radius only keeps more pairs, so every dropped contribution stays below
+ * the cutoff. */
+static double cull_radius(const double* w, double cutoff, double k_sigma, int g, int n_parents,
+                          double child_k_min) {
+  double r = cutoff_radius(w, cutoff, k_sigma);
+  if (g >= n_parents && child_k_min > 0.0 && child_k_min > r) r = child_k_min;
+  return r;
 }
 
 /* Section 3.2, Eq. 3-5, exact real-valued test in FP64.  For each tile t of
@@ -158,7 +173,8 @@ static double cull_radius(const double* w, double cutoff, double k_sigma) {
 void oracle_cull_exact(int N, int Ge, const double* L, const double* m,
                        const double* w, long long Q, const double* x, int tile,
                        int k, const double* proj, double cutoff,
-                       double k_sigma, unsigned char* keep) {
+                       double k_sigma, int n_parents, double child_k_min,
+                       unsigned char* keep) {
   long long T = (Q + tile - 1) / tile;
 #pragma omp parallel for schedule(dynamic, 4)
   for (long long t = 0; t < T; ++t) {
@@ -166,7 +182,7 @@ void oracle_cull_exact(int N, int Ge, const double* L, const double* m,
     for (int g = 0; g < Ge; ++g) {
       const double* Lg = L + (size_t)g * N * N;
       const double* mg = m + (size_t)g * N;
-      double kg = cull_radius(w + (size_t)g * 3, cutoff, k_sigma);
+      double kg = cull_radius(w + (size_t)g * 3, cutoff, k_sigma, g, n_parents, child_k_min);
       int ok = kg >= 0.0;
       for (int j = 0; ok && j < k; ++j) {
         const double* r = proj + (size_t)j * N;
@@ -331,6 +347,7 @@ long long oracle_cull_contract(int N, int Ge, const double* L, const double* m,
                                const double* w, long long Q, const double* x,
                                int tile, int k, const double* proj,
                                double cutoff, double k_sigma, int B,
+                               int n_parents, double child_k_min,
                                long long n_sel, const long long* sel,
                                const double* xc, long long* offsets, int* ids) {
   long long T = (Q + tile - 1) / tile;
@@ -383,7 +400,8 @@ long long oracle_cull_contract(int N, int Ge, const double* L, const double* m,
       for (int i = 0; i < N; ++i) mf[i] = (float)m[(size_t)g * N + i];
       for (int c = 0; c < 3; ++c) { wf[c] = (float)w[(size_t)g * 3 + c]; wd[c] = wf[c]; }
     }
-    double kgd = cull_radius(wd, (double)(float)cutoff, (double)(float)k_sigma);
+    double kgd = cull_radius(wd, (double)(float)cutoff, (double)(float)k_sigma, g, n_parents,
+                             (double)(float)child_k_min);
     key[0] = kgd >= 0.0;
     float kg = (float)kgd;
     for (int j = 0; key[0] && j < k; ++j) {

@@ -20,6 +20,12 @@ PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
 
 # (what the mistake is, the passage it breaks, original text, planted text)
 MUTATIONS = [
+    ("children lose the radius floor", "Section 3.3 (R7)",
+     "  if (g >= n_parents && child_k_min > 0.0 && child_k_min > r) r = child_k_min;",
+     ""),
+    ("radius floor applied to parents instead of children", "Section 3.3 (R7)",
+     "  if (g >= n_parents && child_k_min > 0.0 && child_k_min > r) r = child_k_min;",
+     "  if (g < n_parents && child_k_min > 0.0 && child_k_min > r) r = child_k_min;"),
     ("off-diagonal activation 2 sig - 1 -> sig - 1", "Eq. 2",
      "else if (j < i) v = 2.0 / (1.0 + exp(-th[PIDX(i, j)])) - 1.0;",
      "else if (j < i) v = 1.0 / (1.0 + exp(-th[PIDX(i, j)])) - 1.0;"),

@@ -414,6 +414,74 @@ def test_cull_exact_is_tight_in_one_dimension(oracle):
     assert 0 < keep.sum() < keep.size
 
 
+def test_child_radius_floor_in_one_dimension(oracle):
+    """Reading R7 of Section 3.3: a child (evaluated index >= n_parents)
+    keeps a radius of at least child_k_min sigma, also when its largest
+    weight is below the cutoff (it starts negligible and must still be
+    optimised where it spans its parent); parents keep the cutoff radius.
+    N = 1 with one query per tile makes the test exact: a dim child is kept
+    exactly within child_k_min sigma of its mean, a bright child where its
+    contribution reaches the cutoff or within child_k_min sigma, whichever
+    is wider, a dim parent nowhere; without the floor a dim child is kept
+    nowhere."""
+    r = np.random.default_rng(13)
+    G, Q, cutoff, kmin = 24, 500, 1.0 / 255.0, 3.0
+    sig = np.exp(r.uniform(np.log(0.02), np.log(0.3), size=2 * G))
+    # per group (parents, children): a third dim, a third just above the
+    # cutoff (cutoff radius below kmin), a third bright (radius above kmin)
+    wmax = np.concatenate([r.uniform(1e-4, 3e-3, G // 3), r.uniform(5e-3, 2e-2, G // 3),
+                           r.uniform(0.3, 1.0, G - 2 * (G // 3))])
+    wmax = np.concatenate([wmax, r.permutation(wmax)])
+    w = wmax[:, None] * np.array([[1.0, 0.5, 0.25]])
+    L = sig.reshape(-1, 1, 1)
+    m = r.uniform(-1, 1, size=(2 * G, 1))
+    x = np.linspace(-1.3, 1.3, Q).reshape(Q, 1)
+    proj = np.array([[1.0]])
+    keep = oracle.cull_exact(L, m, w, x, 1, proj, cutoff, 3.0, n_parents=G, child_k_min=kmin)
+    plain = oracle.cull_exact(L, m, w, x, 1, proj, cutoff, 3.0)
+    dist = np.abs(x - m[:, 0][None, :]) / sig[None, :]            # [Q, Ge] in sigmas
+    kcut = np.where(wmax > cutoff, np.sqrt(2.0 * np.log(np.maximum(wmax, cutoff) / cutoff)), -1.0)
+    radius = np.concatenate([kcut[:G], np.maximum(kcut[G:], kmin)])
+    clear = np.abs(dist / np.maximum(radius, 1e-9)[None, :] - 1.0) > 1e-9
+    want = dist <= radius[None, :]
+    assert np.array_equal(keep[clear].astype(bool), want[clear])
+    # parents: the floor changes nothing; dim children: kept only with it
+    assert np.array_equal(keep[:, :G], plain[:, :G])
+    dim_child = G + np.nonzero(wmax[G:] <= cutoff)[0]
+    assert dim_child.size and keep[:, dim_child].any() and not plain[:, dim_child].any()
+    # every dropped contribution stays below the cutoff
+    contrib = wmax[None, :] * np.exp(-0.5 * dist ** 2)
+    assert np.all(contrib[keep == 0] < cutoff)
+
+
+def test_child_radius_floor_contract_is_conservative(oracle):
+    """With children and the radius floor, the FP32 contract keeps every pair
+    the exact test keeps (6-D, several projections), the dim children are
+    evaluated, and every dropped pair's contribution is below the cutoff."""
+    tile, cutoff = 64, 1.0 / 255.0
+    mix, x, proj = _cull_case(seed=4, G=40)
+    ch = synth.children(6, 40, 5, spread=0.05, brightness=(0.0009, 0.0011))
+    L, m, w = oracle.activate(raw_from(oracle, mix, ch))
+    G = 40
+    keep = oracle.cull_exact(L, m, w, x, tile, proj, cutoff, 3.0, n_parents=G, child_k_min=3.0)
+    offs, ids = oracle.cull_contract(L, m, w, x, tile, proj, cutoff, 3.0, 64, n_parents=G,
+                                     child_k_min=3.0)
+    T, Ge = keep.shape
+    contract = np.zeros_like(keep)
+    for t in range(T):
+        contract[t, ids[offs[t]:offs[t + 1]]] = 1
+    assert np.all(contract >= keep)
+    assert keep[:, G:].any(), "children below the cutoff must be evaluated somewhere"
+    for g in range(Ge):
+        A = np.linalg.inv(L[g] @ L[g].T)
+        d = x - m[g]
+        s = np.einsum("qi,ij,qj->q", d, A, d).reshape(T, tile)
+        contrib = w[g].max() * np.exp(-0.5 * s)
+        assert np.all(contrib[contract[:, g] == 0] < cutoff)
+        if g >= G:  # inside 3 sigma of a child: kept
+            assert np.all(contract[:, g][(s <= 9.0).any(axis=1)] == 1)
+
+
 def test_cull_sound_for_correlated_factors(oracle):
     """Strongly correlated factors (off-diagonals near +-1, small diagonals):
     the projected width must be |L^T r| (r^T V r), and one query per tile
