@@ -42,18 +42,19 @@ G, Q = WORKLOADS["fit_n6"]
 
 
 def workload_name(g, q):
-    return (f"N={N_DIM} culled fit step: {g} Gaussians (+{g} children at brightness t/10), "
+    return (f"N={N_DIM} culled fit step: {g} Gaussians (+{g} children at brightness t/10, "
+            "evaluated within 3 sigma), "
             f"Q=2^{q.bit_length() - 1} Morton-tiled queries, tile {TILE}, k={K_PROJ} projections, "
             f"cutoff 1/255, {BUCKETS} buckets, Adam lr 1e-3")
 
 
 # DRAM bytes per candidate entry of one bwd_h_kernel<6> launch:
-# dram__bytes_read.sum + dram__bytes_write.sum = 19.58 MB + 299.93 MB from one
-# ncu capture of the 1/8 workload (about 2.76 million entries), i.e. 115.8 B
-# per entry; a full launch's traffic is this times its entries (the kernel
-# streams one gradient record per entry, so traffic grows in proportion).  To
-# be re-taken whenever the kernel changes.
-BWD_BYTES_PER_ENTRY = (19.579904e6 + 299.926016e6) / 2760083
+# dram__bytes_read.sum + dram__bytes_write.sum = 36.69 MB + 621.15 MB from one
+# ncu capture of the 1/8 workload (5,211,201 entries), i.e. 126.2 B per entry;
+# a full launch's traffic is this times its entries (the kernel streams one
+# gradient record per entry, so traffic grows in proportion).  To be re-taken
+# whenever the kernel changes.
+BWD_BYTES_PER_ENTRY = (36.690944e6 + 621.153792e6) / 5211201
 
 
 def flops_per_pair(N: int):
@@ -70,13 +71,14 @@ def tc_flops_per_pair(N: int):
     """Tensor-core flops per pair.  Algorithmic (the lifted contraction
     counted once): forward 2F (s = phi . coef), backward 4F (s recomputed and
     the gradient contraction sum_q beta phi), F = N(N+1)/2 + N + 1.
-    Executed by the kernels (FP16 hi/lo split, three products, K padded to
-    KP = 16 ceil(F / 16)): forward 6 KP; backward 6 KP for S plus 18 KP for
-    D2 = E Psi (Psi has 3 KP columns, one block per colour)."""
+    Executed by the kernels (FP16 hi/lo split, K padded to KP = 16 ceil(F /
+    16)): forward 6 KP (three products); backward 6 KP for S (three
+    products) plus 12 KP for D2 = E Psi (E single FP16, Psi hi/lo: two
+    products; Psi has 3 KP columns, one block per colour)."""
     P = N * (N + 1) // 2
     F = P + N + 1
     KP = (F + 15) // 16 * 16
-    return 2 * F, 4 * F, 6 * KP, 6 * KP + 18 * KP
+    return 2 * F, 4 * F, 6 * KP, 6 * KP + 12 * KP
 
 
 def fp32_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
@@ -156,7 +158,9 @@ def build_workload(device):
     x = torch.as_tensor(c["x"]).to(device)
     target = torch.as_tensor(c["target"]).to(device)
     proj = torch.as_tensor(c["proj"]).to(device)
-    cp = ndg.CullParams(K_PROJ, proj, CUTOFF, 3.0, BUCKETS)
+    # children below the cutoff keep a 3-sigma radius (Section 3.3): they are
+    # evaluated, and optimised, where they span their parents
+    cp = ndg.CullParams(K_PROJ, proj, CUTOFF, 3.0, BUCKETS, child_k_min=3.0)
     return c, ch, gm, x, target, cp
 
 
@@ -241,7 +245,8 @@ def cpu_baseline(c, ch, seconds: float = 15.0, single_seconds: float = 0.0):
     raw = oracle.Raw.from_arrays([c["mix"][n] for n in names[:4]] + [ch[n] for n in names[4:]], True)
     x = c["x"].astype(np.float64)
     L, m, w = oracle.activate(raw)
-    offs, ids = oracle.cull_contract(L, m, w, x, TILE, c["proj"], CUTOFF, 3.0, BUCKETS)
+    offs, ids = oracle.cull_contract(L, m, w, x, TILE, c["proj"], CUTOFF, 3.0, BUCKETS,
+                                     n_parents=int(c["mix"]["mean"].shape[0]), child_k_min=3.0)
     T = len(offs) - 1
     rng = np.random.default_rng(0)
     order = rng.permutation(T)
@@ -574,10 +579,11 @@ def run_fit_n10(device, steps: int = 5000, pool: int = 8, time_cap_s: float = 54
     from paper_2405_20067_gb300.train import Trainer
     c = synth.config3()
     N = c["N"]
-    # the paper's fixed 3-sigma cull: a contribution cutoff above the
-    # children's starting brightness (t / 10) would cull them everywhere, so
-    # they would get no gradient and never materialise
-    cp = ndg.CullParams(K_PROJ, torch.as_tensor(c["proj"]).to(device), 0.0, 3.0, BUCKETS)
+    # contribution cutoff 1/255 with the children's 3-sigma radius floor
+    # (Section 3.3): children start at brightness t/10, below the cutoff, and
+    # are still evaluated and optimised where they span their parents
+    cp = ndg.CullParams(K_PROJ, torch.as_tensor(c["proj"]).to(device), CUTOFF, 3.0, BUCKETS,
+                        child_k_min=3.0)
     # pre-evaluated pool: queries on planes, targets from the ground truth
     gt = ndg.Mixture.from_arrays(N, c["gt"], device=device)
     xs, ts = [], []
@@ -617,7 +623,8 @@ def run_fit_n10(device, steps: int = 5000, pool: int = 8, time_cap_s: float = 54
     assert tr.check() == ndg.NDG_OK
     return {"workload": "N=10 fit: 2M-Gaussian ground truth, 50k parents -> <= 1M, 2^18-query "
                         f"minibatches from a pool of {pool}, Adam lr 1e-3, refinement every 300 "
-                        "steps, fixed 3-sigma cull, graph-captured step (tensor-core forward, "
+                        "steps, cutoff 1/255 with a 3-sigma radius floor for children, "
+                        "graph-captured step (tensor-core forward, "
                         "FP32 backward); each capture runs two extra warm-up steps",
             "steps": done, "wall_s": round(wall, 2), "ms_per_step": round(wall / done * 1e3, 2),
             "loss_curve": curve, "G": growth}
@@ -720,8 +727,9 @@ def main():
                     "algorithmic": f"{alg_bwd} flop/pair (4F: recompute s, gradient contraction)",
                     "executed_tflops": round(executed, 2),
                     "executed_frac": round(executed / tc_peak, 4),
-                    "executed_note": f"{exe_bwd} MMA flop/pair issued: FP16 hi/lo split (3 "
-                                     "products) and the colour-blocked Psi operand",
+                    "executed_note": f"{exe_bwd} MMA flop/pair issued: S from FP16 hi/lo (3 "
+                                     "products), E Psi from single-FP16 E and hi/lo Psi (2 "
+                                     "products) with the colour-blocked Psi operand",
                     "tensor_frac": round(achieved / tc_peak, 4)}
         mufu_frac = mean_pairs / t_bwd / probe["ex2"]["per_s"]
         roofline["mufu"] = {"achieved": mean_pairs / t_bwd, "peak": probe["ex2"]["per_s"],
@@ -739,7 +747,7 @@ def main():
                     "frac": round(achieved / fp32_peak, 4), "traffic": None,
                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz "
                                    f"(clock from {peak_kind} peaks file)"}
-    kernels["backward"]["form"] = ("tensor-core (tcgen05 FP16x3, E Psi contraction)"
+    kernels["backward"]["form"] = ("tensor-core (tcgen05; S FP16x3, E Psi FP16x2)"
                                    if args.bwd_form == "tc" else "FP32 per-pair partials")
     kernels["backward"]["fp32_equiv_tflops"] = round(mean_pairs * bwd_f / t_bwd / 1e12, 3)
     kernels["forward"]["form"] = "lifted tensor-core (tcgen05 FP16x3)"

@@ -104,6 +104,14 @@ typedef struct {
   float cutoff;
   float k_sigma;
   int buckets;
+  /* Section 3.3: a child (evaluated index >= G) starts with a negligible
+   * contribution spanning its parent and is optimised until it
+   * materialises; with child_k_min > 0 its radius is at least child_k_min
+   * (e.g. the 3 of Eq. 5) even when its largest weight is below the cutoff,
+   * so that it is evaluated, and receives a gradient, where it spans the
+   * parent (a wider radius only keeps more pairs: every dropped contribution
+   * stays below the cutoff).  0: no floor. */
+  float child_k_min;
 } ndg_cull_params;
 
 /* Candidate lists as CSR over tiles.  Caller-owned device buffers:

@@ -57,6 +57,7 @@ ndg_status check_cull_params(const ndg_cull_params* cp) {
   if (cp->buckets < 1 || cp->buckets > NDG_MAX_BUCKETS) return NDG_ERR_INVALID_ARG;
   if (!(cp->cutoff >= 0.0f) || !std::isfinite(cp->cutoff)) return NDG_ERR_INVALID_ARG;
   if (!(cp->cutoff > 0.0f) && !(cp->k_sigma >= 0.0f)) return NDG_ERR_INVALID_ARG;
+  if (!(cp->child_k_min >= 0.0f) || !std::isfinite(cp->child_k_min)) return NDG_ERR_INVALID_ARG;
   return NDG_OK;
 }
 
@@ -301,6 +302,7 @@ ndg_status build_cull(const ndg_mixture* mix, const ndg_queries* q, const ndg_cu
   pa.proj = cp->proj;
   pa.cutoff = cp->cutoff;
   pa.k_sigma = cp->k_sigma;
+  pa.child_k_min = cp->child_k_min;
   pa.range = range;
   pa.gkey = k > 0 ? gkey : nullptr;
   pa.bin = (uint32_t*)(w + L.bin);

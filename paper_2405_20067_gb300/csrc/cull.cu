@@ -357,15 +357,23 @@ __global__ void __launch_bounds__(128) prep_kernel(PrepArgs a) {
       if (cond) live = live && condition_gaussian<N>(L, m, wf, a.xc, cmu, cT, cw);
     }
     // Cull radius: k_sigma, or sqrt(2 ln(w_max / cutoff)) from the FP32
-    // weights (conditioned: the conditional weights) in FP64, rounded once.
+    // weights (conditioned: the conditional weights) in FP64, rounded once;
+    // a child keeps at least child_k_min (Section 3.3: it is optimised while
+    // negligible), also below the cutoff.
     float kg;
+    bool reach = true;
     if (a.cutoff > 0.0f) {
       float wm = cond ? fmaxf(fmaxf(cw[0], cw[1]), cw[2]) : fmaxf(fmaxf(wf[0], wf[1]), wf[2]);
       if (wm > a.cutoff) kg = (float)sqrt(2.0 * log((double)wm / (double)a.cutoff));
-      else { kg = -1.0f; live = false; }
+      else { kg = -1.0f; reach = false; }
     } else {
       kg = a.k_sigma;
     }
+    if (child && a.child_k_min > 0.0f && a.child_k_min > kg) {
+      kg = a.child_k_min;
+      reach = true;
+    }
+    live = live && reach;
     uint8_t klo[NDG_MAX_K], khi[NDG_MAX_K];
     int blo0 = 0, bhi0 = 0;
     for (int j = 0; j < a.k && live; ++j) {

@@ -111,6 +111,12 @@ __global__ void __launch_bounds__(128) fwd_kernel(FwdArgs a) {
       for (int i = 0; i < 3; ++i) dst[2 * (P + N + i)] = w[i];
     }
     __syncthreads();
+    // two-level summation: the stage's contributions are summed on their own
+    // and the stage sum is added to the running total, so that the rounding
+    // error grows with the stage length plus the number of stages, not with
+    // the tile's whole candidate count (tens of thousands at the benchmark's
+    // density)
+    float2 pa[3] = {f2(0.f), f2(0.f), f2(0.f)}, pb[3] = {f2(0.f), f2(0.f), f2(0.f)};
     const int npairs = (n + 1) >> 1;
     for (int p = 0; p < npairs; ++p) {
       const float2* r = reinterpret_cast<const float2*>(spair + p * RR);
@@ -131,9 +137,14 @@ __global__ void __launch_bounds__(128) fwd_kernel(FwdArgs a) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const float2 wc = r[P + N + c];
-        acca[c] = __ffma2_rn(wc, ea, acca[c]);
-        accb[c] = __ffma2_rn(wc, eb, accb[c]);
+        pa[c] = __ffma2_rn(wc, ea, pa[c]);
+        pb[c] = __ffma2_rn(wc, eb, pb[c]);
       }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acca[c] = __fadd2_rn(acca[c], pa[c]);
+      accb[c] = __fadd2_rn(accb[c], pb[c]);
     }
     __syncthreads();
   }

@@ -17,6 +17,7 @@ struct PrepArgs {
   int k, KP, B;
   const float* proj;
   float cutoff, k_sigma;
+  float child_k_min;   // children's radius floor (Section 3.3), 0: none
   const float* range;  // lo, hi, inv_h, NDG_MAX_K each
   uint8_t* gkey;       // [Ge][2 KP] or null
   uint32_t* bin;       // [Ge] or null

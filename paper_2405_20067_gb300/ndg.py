@@ -60,7 +60,8 @@ class QueriesC(ctypes.Structure):
 
 class CullParamsC(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("proj", _P), ("cutoff", ctypes.c_float),
-                ("k_sigma", ctypes.c_float), ("buckets", ctypes.c_int)]
+                ("k_sigma", ctypes.c_float), ("buckets", ctypes.c_int),
+                ("child_k_min", ctypes.c_float)]
 
 
 class CullC(ctypes.Structure):
@@ -265,9 +266,11 @@ class CullParams:
     cutoff: float
     k_sigma: float = 3.0
     buckets: int = 64
+    child_k_min: float = 0.0  # children's radius floor (Section 3.3); 0: none
 
     def c(self) -> CullParamsC:
-        return CullParamsC(self.k, _ptr(self.proj), self.cutoff, self.k_sigma, self.buckets)
+        return CullParamsC(self.k, _ptr(self.proj), self.cutoff, self.k_sigma, self.buckets,
+                           self.child_k_min)
 
 
 def queries_c(x: torch.Tensor, tile: int) -> QueriesC:

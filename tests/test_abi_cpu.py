@@ -74,6 +74,7 @@ def test_invalid_arguments_rejected_on_host(ndg):
         (_mix_c(ndg), q, ndg.CullParamsC(4, None, 0.0, 3.0, 64)),                      # proj NULL
         (_mix_c(ndg), q, ndg.CullParamsC(4, ctypes.c_void_p(0x3000), 0.0, 3.0, 256)),  # B > 255
         (_mix_c(ndg), q, ndg.CullParamsC(4, ctypes.c_void_p(0x3000), -1.0, 3.0, 64)),  # cutoff < 0
+        (_mix_c(ndg), q, ndg.CullParamsC(4, ctypes.c_void_p(0x3000), 0.0, 3.0, 64, -1.0)),  # floor < 0
     ]
     for m, qq, cc in cases:
         st = L.ndg_build_cull(ctypes.byref(m), ctypes.byref(qq), ctypes.byref(cc),

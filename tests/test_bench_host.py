@@ -11,10 +11,11 @@ def test_fp32_flops_per_pair():
 
 
 def test_tensor_core_flops_per_pair():
-    # N = 6: F = 21 + 6 + 1 = 28 lifted features, K padded to 32
-    assert bench.tc_flops_per_pair(6) == (56, 112, 192, 768)
+    # N = 6: F = 21 + 6 + 1 = 28 lifted features, K padded to 32; backward
+    # S: 3 products x 2 x 32; E Psi: 2 products x 2 x (3 x 32)
+    assert bench.tc_flops_per_pair(6) == (56, 112, 192, 192 + 384)
     # N = 10: F = 55 + 10 + 1 = 66, K padded to 80
-    assert bench.tc_flops_per_pair(10) == (132, 264, 480, 1920)
+    assert bench.tc_flops_per_pair(10) == (132, 264, 480, 480 + 960)
     # F a multiple of 16: no padding (N = 1: F = 3 -> 16)
     assert bench.tc_flops_per_pair(1)[2] == 6 * 16
 

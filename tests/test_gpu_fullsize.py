@@ -6,7 +6,8 @@ The oracle cannot evaluate these workloads whole in seconds, so each check
 samples what the oracle can compute one by one:
 
 * config 1 (N = 6 fit step: 100,000 parents + 100,000 children at brightness
-  t/10, 2^20 Morton-tiled queries): the candidate lists of all 4,096 tiles
+  t/10, below the cutoff but evaluated within 3 sigma, 2^20 Morton-tiled
+  queries): the candidate lists of all 4,096 tiles
   bit-exact; the outputs of 48 sampled tiles; the gradients of 64 sampled
   parents.  With dy fixed, a Gaussian's gradient involves only its own
   pairs, so the oracle differentiates the mixture restricted to the sampled
@@ -16,8 +17,9 @@ samples what the oracle can compute one by one:
 * config 2 (N = 10, 500,000 Gaussians, 2^22 queries on 256 planes): the
   lists of 6 sampled tiles bit-exact (the oracle runs the contract for those
   tiles only) and their outputs.
-* config 3 (N = 10 fit: 50,000 parents, 2^18-query minibatch, targets from
-  a 2M-Gaussian ground truth): gradients of 48 sampled parents (FP32
+* config 3 (N = 10 fit: 50,000 parents with children evaluated within 3
+  sigma, 2^18-query minibatch, targets from a 2M-Gaussian ground truth):
+  gradients of 48 sampled parents (FP32
   backward, N > 6), graph replays equal eager steps, the loss decreases.
 * config 4 (batched render specs): three of the 64 frames (the largest, the
   smallest, one N = 8), outputs of sampled tiles including the ragged edges.
@@ -31,6 +33,7 @@ from paper_2405_20067_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 TILE, K, CUTOFF, KS, B = 256, 16, 1.0 / 255.0, 3.0, 64
+KMIN = 3.0  # children's radius floor (Section 3.3, reading R7), as bench.py
 
 
 @pytest.fixture(scope="module")
@@ -108,13 +111,14 @@ def cfg1(ndg, oracle):
     ch = synth.children(N, G, 11, spread=0.05, brightness=(0.0009, 0.0011))
     gm = ndg.Mixture.from_arrays(N, c["mix"], ch, G_cap=G + G // 10)
     x = torch.as_tensor(c["x"]).cuda()
-    cp = ndg.CullParams(K, torch.as_tensor(c["proj"]).cuda(), CUTOFF, KS, B)
+    cp = ndg.CullParams(K, torch.as_tensor(c["proj"]).cuda(), CUTOFF, KS, B, child_k_min=KMIN)
     ev = ndg.Evaluator(gm, x, TILE, cp)
     E = ev.build(gm)
     raw = oracle_raw(oracle, c["mix"], ch)
     L, m, w = oracle.activate(raw)
     xd = c["x"].astype(np.float64)
-    o_offs, o_ids = oracle.cull_contract(L, m, w, xd, TILE, c["proj"], CUTOFF, KS, B)
+    o_offs, o_ids = oracle.cull_contract(L, m, w, xd, TILE, c["proj"], CUTOFF, KS, B,
+                                         n_parents=G, child_k_min=KMIN)
     return dict(N=N, G=G, Q=Q, c=c, ch=ch, gm=gm, x=x, xd=xd, ev=ev, E=E, L=L, m=m, w=w,
                 o_offs=o_offs, o_ids=o_ids)
 
@@ -234,7 +238,7 @@ def test_config3_fit_full_size(ndg, oracle):
     N, G = c["N"], c["mix"]["mean"].shape[0]
     x = torch.as_tensor(c["x"]).cuda()
     Q = x.shape[0]
-    cp = ndg.CullParams(K, torch.as_tensor(c["proj"]).cuda(), CUTOFF, KS, B)
+    cp = ndg.CullParams(K, torch.as_tensor(c["proj"]).cuda(), CUTOFF, KS, B, child_k_min=KMIN)
     gt = ndg.Mixture.from_arrays(N, c["gt"])
     ev_gt = ndg.Evaluator(gt, x, TILE, cp, backward=False)
     ev_gt.build(gt)
@@ -255,7 +259,8 @@ def test_config3_fit_full_size(ndg, oracle):
     L, m, w = oracle.activate(raw)
     xd = c["x"].astype(np.float64)
     T = ev.T
-    o_offs, o_ids = oracle.cull_contract(L, m, w, xd, TILE, c["proj"], CUTOFF, KS, B)
+    o_offs, o_ids = oracle.cull_contract(L, m, w, xd, TILE, c["proj"], CUTOFF, KS, B,
+                                         n_parents=G, child_k_min=KMIN)
     assert np.array_equal(offs.cpu().numpy(), o_offs)
     assert torch.equal(ids, torch.as_tensor(o_ids).cuda())
     par, chd = raw_rows(c["mix"], c["children"], S)

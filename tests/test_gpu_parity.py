@@ -507,3 +507,56 @@ def test_non_finite_parameter_sets_numeric_status(ndg):
     gm.c_color_raw.view(-1)[7] = float("-inf")
     ev.forward(gm, mode=ndg.NDG_MODE_TC)
     assert ndg.read_status(ev.ws) == 0
+
+
+@pytest.mark.parametrize("N,tile,conditioned", [(6, 256, False), (10, 128, False), (6, 256, True)])
+def test_children_below_cutoff_keep_radius_floor(ndg, oracle, N, tile, conditioned):
+    """Section 3.3 with a contribution cutoff (reading R7): children start at
+    brightness t/10 = 1e-3, below the 1/255 cutoff, and keep a radius of 3
+    sigma (child_k_min) so that they are evaluated where they span their
+    parents.  Lists bit-exact against the oracle's contract with the same
+    floor, children present in them (absent without the floor), forward
+    within tolerance in both forms."""
+    import torch
+    G, Q, k = 800, 12000, 16
+    seed = 950 + N + int(conditioned)
+    mix = synth.mixture(N, G, seed)
+    ch = synth.children(N, G, seed + 1, spread=0.05, brightness=(0.0009, 0.0011))
+    xc = None
+    if conditioned:
+        xc_np = synth.rng(seed + 4).uniform(-0.5, 0.5, size=N - 3).astype(np.float32)
+        xp = synth.queries_box(3, Q, seed + 2)
+        x = np.concatenate([xp, np.repeat(xc_np[None, :], Q, axis=0)], axis=1).astype(np.float32)
+        xc = torch.as_tensor(xc_np).cuda()
+    else:
+        x = synth.queries_box(N, Q, seed + 2)
+    gm = ndg.Mixture.from_arrays(N, mix, ch)
+    xt = torch.as_tensor(x).cuda()
+    proj = synth.projections(N, k, seed + 3)
+    raw = oracle_raw(oracle, mix, ch)
+    L, m, w = oracle.activate(raw)
+    xd = x.astype(np.float64)
+    sets = {}
+    for floor in (0.0, 3.0):
+        cp = ndg.CullParams(k, torch.as_tensor(proj).cuda(), 1 / 255, 3.0, 64, child_k_min=floor)
+        ev = ndg.Evaluator(gm, xt, tile, cp)
+        E = ev.build(gm, xc=xc)
+        offs, ids = oracle.cull_contract(L, m, w, xd, tile, proj, 1 / 255, 3.0, 64,
+                                         xc=None if xc is None else xc.cpu().numpy(),
+                                         n_parents=G, child_k_min=floor)
+        assert E == offs[-1], (floor, E, offs[-1])
+        g_off = ev.cull.offsets.cpu().numpy()
+        g_ids = ev.cull.ids[:E].cpu().numpy()
+        assert np.array_equal(g_off, offs)
+        for t, (a, b) in enumerate(zip(csr_sets(g_off, g_ids), csr_sets(offs, ids))):
+            assert np.array_equal(a, b), f"floor {floor} tile {t}"
+        sets[floor] = (E, int((g_ids >= G).sum()))
+        for mode, tol in ((ndg.NDG_MODE_FP32, 1e-5), (ndg.NDG_MODE_TC, 1e-3)):
+            y = ev.forward(gm, mode=mode).cpu().numpy()
+            yo = oracle.eval(L, m, w, xd, tile, offs, ids)
+            assert_outputs_close(y, yo, rtol=tol, floor=1e-3)
+        assert ndg.read_status(ev.ws) == 0
+    assert sets[0.0][1] == 0, "children below the cutoff must be culled without the floor"
+    assert sets[3.0][1] > 0, "with the floor the children must be evaluated"
+    print(f"N={N} conditioned={conditioned}: entries {sets[0.0][0]} -> {sets[3.0][0]} "
+          f"({sets[3.0][1]} child entries)")

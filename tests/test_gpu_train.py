@@ -107,3 +107,48 @@ def test_graph_replay_matches_eager_steps(ndg, mode):
         if pa is not None:
             assert torch.equal(pa.detach(), pb.detach()), f
             assert torch.equal(getattr(a.m1, f), getattr(b.m1, f)), f
+
+
+def test_children_grow_and_materialise_under_cutoff(ndg, oracle):
+    """Section 3.3 under a contribution cutoff: with the children's radius
+    floor (reading R7) the children, created at brightness t/10 below the
+    1/255 cutoff, receive gradients during the fit, some grow past t, and
+    the refinement materialises them; the refinement matches the oracle's
+    on the same raw parameters."""
+    import math
+    import torch
+    from helpers import NAMES, oracle_raw
+    from paper_2405_20067_gb300.train import Trainer
+    N, G, Q = 6, 300, 8192
+    gt = ndg.Mixture.from_arrays(N, synth.mixture(N, 150, 60))
+    x = torch.as_tensor(synth.queries_box(N, Q, 61)).cuda()
+    evg = ndg.Evaluator(gt, x, 256, ndg.CullParams(0, None, 0.0, 3.0, 1), E_cap=64 * 150 + 16)
+    evg.build(gt)
+    target = evg.forward(gt).clone()
+    gm = ndg.Mixture.from_arrays(N, synth.mixture(N, G, 62), G_cap=3 * G)
+    cp = ndg.CullParams(8, torch.as_tensor(synth.projections(N, 8, 63)).cuda(), 1 / 255, 3.0, 64,
+                        child_k_min=3.0)
+    t = 0.01
+    tr = Trainer(gm, x, target, 256, cp, lr=5e-2, t=t, phase=0)
+    tr.refine()  # first phase: every parent receives a child at brightness ~t/10
+    assert tr.mix.has_children and tr.mix.G == G
+    c0 = tr.mix.c_alpha_raw[:G].detach().clone()
+    for _ in range(150):
+        tr.step(refine=False)
+    tr.check()
+    moved = (tr.mix.c_alpha_raw[:G].detach() - c0).abs()
+    assert float(moved.max()) > 0.5, "children received no gradient"
+    # the refinement against the oracle's on the same raw parameters
+    pm = tr.mix
+    arrays = {n: getattr(pm, n)[:pm.G].detach().cpu().numpy() for n in NAMES}
+    raw = oracle_raw(oracle, {n: arrays[n] for n in NAMES[:4]}, {n: arrays[n] for n in NAMES[4:]})
+    noise = tr.noise.cpu().numpy().astype(np.float64)
+    a_thr = float(np.float32(math.log(t)))
+    new, Gn, flag = oracle.densify(raw, pm.G_cap, a_thr, math.log(t / 10), noise)
+    assert Gn > G, "no child grew past the threshold"
+    tr.refine()
+    assert tr.mix.G == Gn
+    for n in NAMES:
+        got = getattr(tr.mix, n)[:Gn].detach().cpu().numpy().astype(np.float64)
+        np.testing.assert_allclose(got, getattr(new, n)[:Gn], rtol=2e-6, atol=2e-6, err_msg=n)
+    print(f"children materialised: {Gn - G} of {G}")
