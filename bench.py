@@ -393,6 +393,19 @@ def run_fit(form: str, steps: int, warmup: int, device: str, flush, world: int, 
            "pairs_per_step": statistics.mean(pairs), "candidates_per_step": int(tr.ev.cull.E()),
            "kernels_ms": kern, "gpu_launches": int(round(launches_per_step * steps)),
            "graph": graph, "clocks": clk.summary()}
+    if graph:
+        # the same steps launched eagerly, timed exactly like the replays
+        # (flush, events on the stream, synchronise): graph against eager
+        eager_ms = []
+        for i in range(steps):
+            flush.zero_()
+            starts[i].record()
+            one_step(None)
+            ends[i].record()
+            torch.cuda.synchronize()
+            eager_ms.append(starts[i].elapsed_time(ends[i]))
+        res["eager_ms_per_step"] = statistics.mean(eager_ms)
+        tr.check()
     if e2e_steps:
         xh = x.cpu().pin_memory()
         th = target.cpu().pin_memory()
@@ -772,6 +785,7 @@ def main():
                       "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
            "roofline": roofline, "kernels_ms": kernels, "gpu_launches": chosen["gpu_launches"],
            "e2e": chosen["e2e"], "clocks": chosen["clocks"],
+           "eager_ms_per_step": chosen.get("eager_ms_per_step"),
            "pipe_probe": {k: {"per_clk_per_sm": round(v["per_clk_per_sm"], 2),
                               "per_s": v["per_s"]} for k, v in probe.items()}}
     if plain is not None:

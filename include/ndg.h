@@ -202,6 +202,19 @@ ndg_status ndg_loss_l2(long long Q, const float* y, const float* target,
                        float* dy, double* loss_dev, void* ws, size_t ws_bytes,
                        ndg_stream stream, ndg_trace* trace);
 
+/* The plain L2 loss of one shard of a larger query set, for a fit whose
+ * queries are split across processes (one per GPU): the Q outputs given
+ * here are normalised by the whole set's Q_total (>= Q), so that
+ *   loss_dev [1] = sum (y - target)^2 / (3 Q_total)   (this shard's share),
+ *   dy = 2 (y - target) / (3 Q_total)  [Q][3];
+ * the shards' losses and gradients then add up to those of the whole set.
+ * Q_total == Q is ndg_loss_l2.  The paper has no multi-GPU fit; this is the
+ * query-sharded data parallelism of this library (tiles are independent in
+ * the cull and the evaluation, Section 3.2 and Eq. 8). */
+ndg_status ndg_loss_l2_shard(long long Q, long long Q_total, const float* y, const float* target,
+                             float* dy, double* loss_dev, void* ws, size_t ws_bytes,
+                             ndg_stream stream, ndg_trace* trace);
+
 /* Relative L2 loss.  Section 4.1 trains with a relative L2 loss (after
  * Noise2Noise) without printing its form; the reading implemented:
  *   loss = sum (y - target)^2 / (y^2 + eps) / (3Q) written to loss_dev [1]

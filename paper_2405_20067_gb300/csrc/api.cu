@@ -436,6 +436,22 @@ ndg_status ndg_loss_l2(long long Q, const float* y, const float* target, float* 
   return cuda_ok();
 }
 
+ndg_status ndg_loss_l2_shard(long long Q, long long Q_total, const float* y, const float* target,
+                             float* dy, double* loss_dev, void* ws, size_t ws_bytes,
+                             ndg_stream stream, ndg_trace* trace) {
+  if (Q < 0 || Q_total < Q || !loss_dev || (Q > 0 && (!y || !target || !dy)))
+    return NDG_ERR_INVALID_ARG;
+  if (!ws || !aligned(ws, kAlign)) return NDG_ERR_INVALID_ARG;
+  const size_t off = align_up(sizeof(WsHeader));
+  if (ws_bytes < off + kLossParts * sizeof(double)) return NDG_ERR_WORKSPACE;
+  double* part = (double*)((char*)ws + off);
+  Tracer tr(trace, (cudaStream_t)stream);
+  tr.begin();
+  tr += launch_loss(y, target, dy, 3 * Q, part, loss_dev, (cudaStream_t)stream, -1.0, 3 * Q_total);
+  tr.end();
+  return cuda_ok();
+}
+
 ndg_status ndg_loss_rel_l2(long long Q, const float* y, const float* target, float eps, float* dy,
                            double* loss_dev, void* ws, size_t ws_bytes, ndg_stream stream,
                            ndg_trace* trace) {

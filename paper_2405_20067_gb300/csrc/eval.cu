@@ -671,13 +671,14 @@ int launch_fwd(int N, const FwdArgs& a, long long T, cudaStream_t s) {
 }
 
 int launch_loss(const float* y, const float* target, float* dy, long long n, double* part,
-                double* loss, cudaStream_t s, double rel_eps) {
-  const double scale = n > 0 ? 2.0 / (double)n : 0.0;
+                double* loss, cudaStream_t s, double rel_eps, long long norm) {
+  if (norm <= 0) norm = n;  // the mean over these n outputs, or over a larger set
+  const double scale = norm > 0 ? 2.0 / (double)norm : 0.0;
   if (rel_eps >= 0.0)
     loss_kernel<true><<<LOSS_BLOCKS, 256, 0, s>>>(y, target, dy, n, scale, rel_eps, part);
   else
     loss_kernel<false><<<LOSS_BLOCKS, 256, 0, s>>>(y, target, dy, n, scale, rel_eps, part);
-  loss_final_kernel<<<1, LOSS_BLOCKS, 0, s>>>(part, n, loss);
+  loss_final_kernel<<<1, LOSS_BLOCKS, 0, s>>>(part, norm, loss);
   return 2;
 }
 

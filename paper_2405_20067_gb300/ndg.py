@@ -102,7 +102,7 @@ def _tr(trace):
 EXPORTS = ["ndg_workspace_size", "ndg_build_cull", "ndg_build_cull_conditioned", "ndg_forward",
            "ndg_loss_l2", "ndg_loss_rel_l2", "ndg_backward", "ndg_adam", "ndg_densify",
            "ndg_read_status", "ndg_status_string", "ndg_version", "ndg_forward_noalloc",
-           "ndg_selftest_timeout", "ndg_probe_pipe"]
+           "ndg_selftest_timeout", "ndg_probe_pipe", "ndg_loss_l2_shard"]
 NDG_ERR_SCRATCH_LIMIT = 7
 
 
@@ -124,6 +124,8 @@ def lib():
         L.ndg_build_cull_conditioned.argtypes = [M, Qp, CP, _P, C, _P, sz, _P, TR]
         L.ndg_forward.argtypes = [M, Qp, C, ctypes.c_int, _P, _P, sz, _P, TR]
         L.ndg_loss_l2.argtypes = [ctypes.c_longlong, _P, _P, _P, _P, _P, sz, _P, TR]
+        L.ndg_loss_l2_shard.argtypes = [ctypes.c_longlong, ctypes.c_longlong, _P, _P, _P, _P, _P,
+                                        sz, _P, TR]
         L.ndg_loss_rel_l2.argtypes = [ctypes.c_longlong, _P, _P, ctypes.c_float, _P, _P, _P, sz,
                                       _P, TR]
         L.ndg_backward.argtypes = [M, Qp, C, ctypes.c_int, _P, M, _P, sz, _P, TR]
@@ -141,7 +143,7 @@ def lib():
         for name in ["ndg_build_cull", "ndg_build_cull_conditioned", "ndg_forward", "ndg_loss_l2",
                      "ndg_loss_rel_l2", "ndg_backward", "ndg_adam", "ndg_densify",
                      "ndg_read_status", "ndg_forward_noalloc", "ndg_selftest_timeout",
-                     "ndg_probe_pipe"]:
+                     "ndg_probe_pipe", "ndg_loss_l2_shard"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -332,6 +334,15 @@ def loss_l2(y: torch.Tensor, target: torch.Tensor, dy: torch.Tensor, loss: torch
             ws: torch.Tensor, stream=None, trace: Trace | None = None):
     _check(lib().ndg_loss_l2(int(y.shape[0]), _ptr(y), _ptr(target), _ptr(dy), _ptr(loss),
                              _ptr(ws), ws.numel(), _stream(stream), _tr(trace)), "ndg_loss_l2")
+
+
+def loss_l2_shard(y: torch.Tensor, target: torch.Tensor, dy: torch.Tensor, loss: torch.Tensor,
+                  ws: torch.Tensor, Q_total: int, stream=None, trace: Trace | None = None):
+    """Plain L2 of this shard's outputs normalised by the whole query set's
+    Q_total (the shards' losses and gradients add up to the whole set's)."""
+    _check(lib().ndg_loss_l2_shard(int(y.shape[0]), int(Q_total), _ptr(y), _ptr(target), _ptr(dy),
+                                   _ptr(loss), _ptr(ws), ws.numel(), _stream(stream), _tr(trace)),
+           "ndg_loss_l2_shard")
 
 
 def selftest_timeout(which: int, ws: torch.Tensor, stream=None):

@@ -61,14 +61,22 @@ class Trainer:
     def __init__(self, mix: ndg.Mixture, x: torch.Tensor, target: torch.Tensor, tile: int,
                  cp: ndg.CullParams, lr: float = 1e-3, t: float = 0.01, phase: int = 300,
                  E_cap: int | None = None, seed: int = 0, mode: int = ndg.NDG_MODE_FP32,
-                 bwd_mode: int | None = None, loss: str = "l2", rel_eps: float = 1e-2):
+                 bwd_mode: int | None = None, loss: str = "l2", rel_eps: float = 1e-2,
+                 loss_norm_queries: int | None = None):
         """mode / bwd_mode: NDG_MODE_FP32 or NDG_MODE_TC for the forward and
         the backward (the tensor-core backward covers N <= 6); bwd_mode
         defaults to mode.  loss: "l2" (plain) or "rel_l2" (the relative L2 of
-        Section 4.1, squared errors over y^2 + rel_eps)."""
+        Section 4.1, squared errors over y^2 + rel_eps).  loss_norm_queries:
+        these queries are a shard of a set of that many (plain L2 only; see
+        shard.py); grad_hook, when set, is called with the gradient tensors
+        before Adam (the shards' sum)."""
         if loss not in ("l2", "rel_l2"):
             raise ValueError(f"unknown loss {loss!r}")
         self.loss_kind, self.rel_eps = loss, rel_eps
+        if loss_norm_queries is not None and loss != "l2":
+            raise ValueError("a sharded loss is the plain L2")
+        self.loss_norm_queries = loss_norm_queries
+        self.grad_hook = None
         self.mix, self.tile, self.cp, self.mode = mix, tile, cp, mode
         self.bwd_mode = mode if bwd_mode is None else bwd_mode
         self.lr, self.t, self.phase = lr, t, phase
@@ -128,6 +136,9 @@ class Trainer:
             if self.loss_kind == "rel_l2":
                 ndg.loss_rel_l2(y.detach(), self.target, self.dy, self.loss, self.ev.ws,
                                 eps=self.rel_eps, trace=self._tr("loss"))
+            elif self.loss_norm_queries is not None:
+                ndg.loss_l2_shard(y.detach(), self.target, self.dy, self.loss, self.ev.ws,
+                                  self.loss_norm_queries, trace=self._tr("loss"))
             else:
                 ndg.loss_l2(y.detach(), self.target, self.dy, self.loss, self.ev.ws,
                             trace=self._tr("loss"))
@@ -137,6 +148,8 @@ class Trainer:
                            has_children=mix.has_children)
         if not mix.has_children:
             grad.u_theta = grad.m_u = grad.c_alpha_raw = grad.c_color_raw = None
+        if self.grad_hook is not None:
+            self.grad_hook(grad.tensors())
         with torch.no_grad():
             pm = self._detached(mix)
             ndg.adam(pm, grad, self._sync_meta(self.m1), self._sync_meta(self.m2), self.step_dev,

@@ -184,6 +184,35 @@ def test_loss_matches_oracle(ndg, oracle):
     assert_outputs_close(dy.cpu().numpy(), go, rtol=1e-6, floor=1e-12)
 
 
+def test_shard_loss_matches_oracle(ndg, oracle):
+    """ndg_loss_l2_shard: a shard of Q outputs normalised by the whole set's
+    Q_total: its loss is the oracle's loss of the shard times Q / Q_total, dy
+    likewise; two shards add up to the whole set's loss."""
+    import torch
+    r = synth.rng(8)
+    Q_total, Q = 90001, 40000
+    y = r.uniform(0, 2, (Q_total, 3)).astype(np.float32)
+    t = r.uniform(0, 2, (Q_total, 3)).astype(np.float32)
+    ws = ndg.workspace(1 << 16)
+    parts = []
+    for q0, q1 in ((0, Q), (Q, Q_total)):
+        yt, tt = torch.as_tensor(y[q0:q1]).cuda(), torch.as_tensor(t[q0:q1]).cuda()
+        dy = torch.empty_like(yt)
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        ndg.loss_l2_shard(yt, tt, dy, loss, ws, Q_total)
+        lo, go = oracle.loss_l2(y[q0:q1].astype(np.float64), t[q0:q1].astype(np.float64))
+        f = (q1 - q0) / Q_total
+        assert abs(loss.item() - lo * f) <= 1e-12 * lo * f
+        assert_outputs_close(dy.cpu().numpy(), go * f, rtol=1e-6, floor=1e-12)
+        parts.append(loss.item())
+    whole, _ = oracle.loss_l2(y.astype(np.float64), t.astype(np.float64))
+    assert abs(sum(parts) - whole) <= 1e-12 * whole
+    with pytest.raises(ndg.NDGError):  # Q_total below the shard's Q
+        ndg.loss_l2_shard(torch.zeros(10, 3, device="cuda"), torch.zeros(10, 3, device="cuda"),
+                          torch.zeros(10, 3, device="cuda"),
+                          torch.zeros(1, dtype=torch.float64, device="cuda"), ws, 9)
+
+
 def test_relative_loss_matches_oracle(ndg, oracle):
     """Relative L2 (Section 4.1 reading): loss to 1e-12, dy to 1e-6, with
     outputs near zero (where the eps term dominates) included."""
