@@ -372,6 +372,7 @@ def run_fit(form: str, steps: int, warmup: int, device: str, flush, world: int, 
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    eager_ms = []
     with ClockSampler(torch.cuda.current_device()) as clk:
         for i in range(steps):
             flush.zero_()
@@ -383,6 +384,16 @@ def run_fit(form: str, steps: int, warmup: int, device: str, flush, world: int, 
             ends[i].record()
             torch.cuda.synchronize()
             pairs.append(pairs_of(tr.ev.cull, Q, TILE))  # counted outside the timed region
+            if graph:
+                # the same step launched eagerly, timed the same way right
+                # after each replay (untimed for the metric): graph against eager
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                one_step(None)
+                e1.record()
+                torch.cuda.synchronize()
+                eager_ms.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -393,19 +404,8 @@ def run_fit(form: str, steps: int, warmup: int, device: str, flush, world: int, 
            "pairs_per_step": statistics.mean(pairs), "candidates_per_step": int(tr.ev.cull.E()),
            "kernels_ms": kern, "gpu_launches": int(round(launches_per_step * steps)),
            "graph": graph, "clocks": clk.summary()}
-    if graph:
-        # the same steps launched eagerly, timed exactly like the replays
-        # (flush, events on the stream, synchronise): graph against eager
-        eager_ms = []
-        for i in range(steps):
-            flush.zero_()
-            starts[i].record()
-            one_step(None)
-            ends[i].record()
-            torch.cuda.synchronize()
-            eager_ms.append(starts[i].elapsed_time(ends[i]))
+    if eager_ms:
         res["eager_ms_per_step"] = statistics.mean(eager_ms)
-        tr.check()
     if e2e_steps:
         xh = x.cpu().pin_memory()
         th = target.cpu().pin_memory()
@@ -584,8 +584,8 @@ def run_fit_n10(device, steps: int = 5000, pool: int = 8, time_cap_s: float = 54
     (children at brightness t/10, t = 0.01) that may grow to 1M under the
     Section 3.3 refinement every 300 steps, Adam lr 1e-3, minibatches of 2^18
     surface queries (16 planes x 128^2) cycled from a pool of pre-evaluated
-    batches, the whole step captured as a CUDA graph (tensor-core forward,
-    FP32 backward: N > 6).  Reports the loss curve, G(t), ms per step and
+    batches, the whole step captured as a CUDA graph (tensor-core forward and
+    backward).  Reports the loss curve, G(t), ms per step and
     the wall time (stopped at time_cap_s)."""
     import torch
     from paper_2405_20067_gb300 import ndg, synth
@@ -611,7 +611,7 @@ def run_fit_n10(device, steps: int = 5000, pool: int = 8, time_cap_s: float = 54
     torch.cuda.empty_cache()
     mix = ndg.Mixture.from_arrays(N, c["mix"], c["children"], G_cap=c["G_max"], device=device)
     tr = Trainer(mix, xs[0].clone(), ts[0].clone(), TILE, cp, lr=1e-3, t=c["t"], phase=0,
-                 mode=ndg.NDG_MODE_TC, bwd_mode=ndg.NDG_MODE_FP32)
+                 mode=ndg.NDG_MODE_TC, bwd_mode=ndg.NDG_MODE_TC)
     tr.capture(refine_each_step=False)
     curve, growth = [], [(0, int(mix.G))]
     torch.cuda.synchronize()
@@ -637,8 +637,8 @@ def run_fit_n10(device, steps: int = 5000, pool: int = 8, time_cap_s: float = 54
     return {"workload": "N=10 fit: 2M-Gaussian ground truth, 50k parents -> <= 1M, 2^18-query "
                         f"minibatches from a pool of {pool}, Adam lr 1e-3, refinement every 300 "
                         "steps, cutoff 1/255 with a 3-sigma radius floor for children, "
-                        "graph-captured step (tensor-core forward, "
-                        "FP32 backward); each capture runs two extra warm-up steps",
+                        "graph-captured step (tensor-core forward and backward); each "
+                        "capture runs two extra warm-up steps",
             "steps": done, "wall_s": round(wall, 2), "ms_per_step": round(wall / done * 1e3, 2),
             "loss_curve": curve, "G": growth}
 

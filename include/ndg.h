@@ -181,7 +181,7 @@ ndg_status ndg_build_cull_conditioned(const ndg_mixture* mix, const ndg_queries*
                            contraction is dense enough for 128-candidate
                            tensor-core chunks), NDG_MODE_FP32 elsewhere; each
                            tile's outputs equal those of the mode it gets.
-                           backward: NDG_MODE_TC for N <= 6, else FP32 */
+                           backward: NDG_MODE_TC */
 /* Crossover measured on GB300 with full tiles of 256 queries: the two forms
  * take equal time at about 190 candidates per tile for N = 6 and about 110
  * for N = 10. */
@@ -233,9 +233,11 @@ ndg_status ndg_loss_rel_l2(long long Q, const float* y, const float* target,
  * the raw parameters and `cull`; per-Gaussian sums run in a fixed order
  * (no atomics), so results are bit-reproducible.  Requires E < 2^31.
  * mode NDG_MODE_FP32: centred form on the FP32 pipe; NDG_MODE_TC: the
- * lifted form on the tensor cores (the gradients of the lifted coefficients
- * and of w as a second contraction E Psi with Psi = dy (x) phi), available
- * for N <= 6 (shared-memory bound); other N return NDG_ERR_INVALID_ARG. */
+ * lifted form on the tensor cores, every N (for N <= 6 the gradients of the
+ * lifted coefficients and of w come from a second contraction E Psi with
+ * Psi = dy (x) phi; above, from beta Phi with beta = e sum_c dy_c w_c and
+ * dl/dw summed in FP32); NDG_MODE_AUTO: NDG_MODE_TC.  Tensor-core gradients
+ * are within ~3e-4 relative of the FP64 definition per tensor. */
 ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q,
                         const ndg_cull* cull, int mode, const float* dy,
                         ndg_mixture* grad, void* ws, size_t ws_bytes,

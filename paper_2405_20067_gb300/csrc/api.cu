@@ -480,8 +480,8 @@ ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q, const ndg_
                         ndg_stream stream, ndg_trace* trace) {
   ndg_status st;
   if ((st = check_mix(mix)) || (st = check_queries(q)) || (st = check_cull(cull))) return st;
-  if (mode == NDG_MODE_AUTO) mode = mix->N <= 6 ? NDG_MODE_TC : NDG_MODE_FP32;
-  if (mode != NDG_MODE_FP32 && (mode != NDG_MODE_TC || mix->N > 6)) return NDG_ERR_INVALID_ARG;
+  if (mode == NDG_MODE_AUTO) mode = NDG_MODE_TC;
+  if (mode != NDG_MODE_FP32 && mode != NDG_MODE_TC) return NDG_ERR_INVALID_ARG;
   if (!grad || grad->N != mix->N || grad->G != mix->G || grad->has_children != mix->has_children ||
       (st = check_mix(grad)))
     return st ? st : NDG_ERR_INVALID_ARG;
@@ -534,7 +534,10 @@ ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q, const ndg_
   ba.part = (float*)(w + L.part);
   ba.status = pa.status;
   tr.begin();
-  tr += mode == NDG_MODE_TC ? launch_bwd_h(N, ba, z.T, s) : launch_bwd(N, ba, z.T, s);
+  // tensor cores: the E Psi form for N <= 6, the beta form (bwd_hb.cu) above
+  // (its operands fit shared and tensor memory up to N = 12)
+  tr += mode == NDG_MODE_TC ? (N <= 6 ? launch_bwd_h(N, ba, z.T, s) : launch_bwd_hb(N, ba, z.T, s))
+                            : launch_bwd(N, ba, z.T, s);
   tr.end();
   float* gsum = (float*)(w + L.gsum);
   tr += launch_segsum(ba.part, part_floats(N), goff, Ge, sv, gsum, s);

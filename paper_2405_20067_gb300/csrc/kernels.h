@@ -127,6 +127,7 @@ int launch_tile_split(const long long* offsets, long long T, long long min_cand,
 int launch_fwd(int N, const FwdArgs& a, long long T, cudaStream_t s);
 int launch_fwd_tc(int N, const FwdArgs& a, long long T, cudaStream_t s);  // FP16 hi/lo, N <= 12
 int launch_bwd_h(int N, const BwdArgs& a, long long T, cudaStream_t s);   // N <= 6
+int launch_bwd_hb(int N, const BwdArgs& a, long long T, cudaStream_t s);  // beta form, N <= 12
 // n outputs; norm: the count the loss is normalised by (0: n)
 int launch_loss(const float* y, const float* target, float* dy, long long n, double* part,
                 double* loss, cudaStream_t s, double rel_eps = -1.0, long long norm = 0);

@@ -38,8 +38,6 @@ class NDGEval(torch.autograd.Function):
                                            else torch.empty_like(getattr(mix, f))
                                            for f in _PARAMS], has_children=mix.has_children)
         mode = getattr(ev, "bwd_mode", ndg.NDG_MODE_FP32)
-        if mode == ndg.NDG_MODE_TC and mix.N > 6:
-            mode = ndg.NDG_MODE_FP32  # the tensor-core backward covers N <= 6
         ndg.backward(mix, ev.x, ev.tile, ev.cull, dy.contiguous(), grad, ev.ws, mode=mode,
                      trace=getattr(ev, "trace_bwd", None))
         outs = [getattr(grad, f) if (mix.has_children or i < 4) else None
@@ -64,7 +62,7 @@ class Trainer:
                  bwd_mode: int | None = None, loss: str = "l2", rel_eps: float = 1e-2,
                  loss_norm_queries: int | None = None):
         """mode / bwd_mode: NDG_MODE_FP32 or NDG_MODE_TC for the forward and
-        the backward (the tensor-core backward covers N <= 6); bwd_mode
+        the backward; bwd_mode
         defaults to mode.  loss: "l2" (plain) or "rel_l2" (the relative L2 of
         Section 4.1, squared errors over y^2 + rel_eps).  loss_norm_queries:
         these queries are a shard of a set of that many (plain L2 only; see

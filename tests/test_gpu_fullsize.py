@@ -19,8 +19,8 @@ samples what the oracle can compute one by one:
   tiles only) and their outputs.
 * config 3 (N = 10 fit: 50,000 parents with children evaluated within 3
   sigma, 2^18-query minibatch, targets from a 2M-Gaussian ground truth):
-  gradients of 48 sampled parents (FP32
-  backward, N > 6), graph replays equal eager steps, the loss decreases.
+  gradients of 48 sampled parents (FP32 and tensor-core backward), graph
+  replays equal eager steps, the loss decreases.
 * config 4 (batched render specs): three of the 64 frames (the largest, the
   smallest, one N = 8), outputs of sampled tiles including the ragged edges.
 """
@@ -230,8 +230,9 @@ def test_config2_sampled_tiles(ndg, oracle):
 def test_config3_fit_full_size(ndg, oracle):
     """N = 10 fit at full size: targets from the 2M-Gaussian ground truth
     (tensor-core forward); gradients of sampled parents against the oracle
-    (FP32 backward, the tensor-core backward covers N <= 6); CUDA-graph
-    replays equal eager steps; the loss decreases."""
+    (FP32 backward at 1e-4, the tensor-core beta form at 1e-3); CUDA-graph
+    replays equal eager steps (tensor-core forward and backward); the loss
+    decreases."""
     import torch
     from paper_2405_20067_gb300.train import Trainer
     c = synth.config3()
@@ -253,6 +254,8 @@ def test_config3_fit_full_size(ndg, oracle):
     E = ev.build(gm)
     dy = (synth.rng(91).standard_normal((Q, 3)) / (3 * Q)).astype(np.float32)
     grad = ev.backward(gm, torch.as_tensor(dy).cuda(), mode=ndg.NDG_MODE_FP32)
+    grad_tc = ev.backward(gm, torch.as_tensor(dy).cuda(), mode=ndg.NDG_MODE_TC)
+    assert ndg.read_status(ev.ws) == 0
     offs, ids = gpu_lists_ascending(ev, E)
     S = np.sort(synth.rng(92).choice(G, size=48, replace=False))
     raw = oracle_raw(oracle, c["mix"], c["children"])
@@ -268,16 +271,19 @@ def test_config3_fit_full_size(ndg, oracle):
     want = oracle.grad(oracle_raw(oracle, par, chd), xd, TILE, so, si, dy.astype(np.float64))
     got = {n: getattr(grad, n)[torch.as_tensor(S).cuda()].cpu().numpy() for n in NAMES}
     rep = assert_grads_close(got, want, NAMES, rtol=1e-4)
-    print(f"config 3: E = {E} in {T} tiles; 48 parents: "
-          + " ".join(f"{n}={v:.1e}" for n, v in rep.items()))
-    del ev, grad
+    got_tc = {n: getattr(grad_tc, n)[torch.as_tensor(S).cuda()].cpu().numpy() for n in NAMES}
+    rep_tc = assert_grads_close(got_tc, want, NAMES, rtol=1e-3)
+    print(f"config 3: E = {E} in {T} tiles; 48 parents: fp32 "
+          + " ".join(f"{n}={v:.1e}" for n, v in rep.items()) + " | tc "
+          + " ".join(f"{n}={v:.1e}" for n, v in rep_tc.items()))
+    del ev, grad, grad_tc
     torch.cuda.empty_cache()
 
     # graph replays against eager steps, then the loss over 30 replays
     def trainer():
         mix = ndg.Mixture.from_arrays(N, c["mix"], c["children"], G_cap=c["G_max"])
         return Trainer(mix, x, target, TILE, cp, lr=1e-3, t=c["t"], phase=300,
-                       mode=ndg.NDG_MODE_TC, bwd_mode=ndg.NDG_MODE_FP32)
+                       mode=ndg.NDG_MODE_TC, bwd_mode=ndg.NDG_MODE_TC)
 
     eager, graphed = trainer(), trainer()
     # the capture's two warm-up steps are steps too: match them eagerly

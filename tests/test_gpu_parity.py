@@ -135,6 +135,13 @@ GRAD_CASES = [
     (5, 400, 6000, 200, 16, 1 / 255, True, "tc"),
     (3, 200, 3000, 33, 8, 0.0, True, "tc"),
     (1, 100, 1000, 256, 1, 0.0, False, "tc"),
+    # the beta form of the tensor-core backward (N > 6)
+    (7, 300, 4000, 100, 8, 0.0, True, "tc"),
+    (8, 500, 6000, 256, 16, 1 / 255, True, "tc"),
+    (9, 300, 4000, 200, 8, 1 / 255, False, "tc"),
+    (10, 400, 6000, 128, 16, 1 / 255, True, "tc"),
+    (11, 200, 3000, 64, 8, 0.0, True, "tc"),
+    (12, 200, 3000, 256, 16, 1 / 255, False, "tc"),
 ]
 
 
