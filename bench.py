@@ -538,18 +538,26 @@ def run_ablation(device) -> dict:
 def run_render_batch(device, n_frames: int = 64) -> dict:
     """Batched render (64 frame specs: G log-uniform in [1e4, 5e5], N in
     {6, 8, 10}, 256^2 .. 1920 x 1080 pixels, one query per pixel, dims beyond
-    position uniform): per-frame latency of cull + forward (CUDA events, one
-    untimed frame first) with the autotuned configuration, p50 / p99 over
-    the frames, next to the fixed configuration (tensor cores, 256-query
-    tiles).  Frames run one after another; each frame's tiles spread over
-    every SM (one CTA per tile)."""
+    position uniform), two ways:
+    - one frame at a time: per-frame latency of cull + forward (CUDA events,
+      one untimed frame first) with the autotuned configuration (median of 5
+      timings per candidate on a class's first frame), p50 / p99 over the
+      frames, next to the fixed configuration (tensor cores, 256-query
+      tiles);
+    - all frames at once: every frame's cull, then one persistent launch of
+      the tensor-core forward over the (frame, tile) work list
+      (ndg_forward_batch).  The device stamps each frame's completion with
+      %globaltimer; p50 / p99 of completion since the launch started, the
+      makespan, and the whole batch (culls + launch) against the sum of the
+      one-at-a-time tensor-core frames.  Every frame's batched output is
+      compared with its own ndg_forward output (bit for bit)."""
     import numpy as np
     import torch
     from paper_2405_20067_gb300 import ndg, synth
-    from paper_2405_20067_gb300.render import Autotuner, Frame, frame_class
+    from paper_2405_20067_gb300.render import Autotuner, Frame, frame_class, render_batch
     specs = synth.config4_frames(n=n_frames)
     tuner = Autotuner()
-    rows = []
+    rows, frames = [], []
     for f in specs:
         N, G, W, H, sd = f["N"], f["G"], f["W"], f["H"], f["seed"]
         gm = ndg.Mixture.from_arrays(N, synth.mixture(N, G, sd), device=device)
@@ -560,22 +568,54 @@ def run_render_batch(device, n_frames: int = 64) -> dict:
         tuned_now = key not in tuner.cache
         cfg = tuner.choose(key, fr.time)
         ms = fr.time(cfg)
-        ms_fixed = fr.time(("tc", 256))
+        ms_fixed = fr.time(("tc", 256))  # leaves the tensor-core output in fr.y
+        fr._ev.pop(128, None)  # keep the 256-query tile state for the batch
         rows.append({"N": N, "G": G, "W": W, "H": H, "config": f"{cfg[0]}/{cfg[1]}",
-                     "tuned_here": tuned_now, "ms": round(ms, 4), "ms_tc256": round(ms_fixed, 4)})
-        fr.release()
-        del fr, gm, x
-        torch.cuda.empty_cache()
+                     "tuned_here": tuned_now, "ms": round(ms, 4), "ms_tc256": round(ms_fixed, 4),
+                     "E": int(fr.evaluator(256).cull.E())})
+        frames.append((fr, fr.y.clone()))
+    torch.cuda.synchronize()
     ms = np.array([r["ms"] for r in rows])
     fx = np.array([r["ms_tc256"] for r in rows])
-    return {"frames": len(rows), "classes_tuned": len(tuner.cache),
-            "candidates": [f"{a}/{b}" for a, b in tuner.candidates],
-            "p50_ms": round(float(np.percentile(ms, 50)), 4),
-            "p99_ms": round(float(np.percentile(ms, 99)), 4),
-            "mean_ms": round(float(ms.mean()), 4),
-            "fixed_tc256_p50_ms": round(float(np.percentile(fx, 50)), 4),
-            "fixed_tc256_p99_ms": round(float(np.percentile(fx, 99)), 4),
-            "pixels": int(sum(r["W"] * r["H"] for r in rows)), "per_frame": rows}
+    out = {"frames": len(rows), "classes_tuned": len(tuner.cache), "tuner_reps": tuner.reps,
+           "candidates": [f"{a}/{b}" for a, b in tuner.candidates],
+           "p50_ms": round(float(np.percentile(ms, 50)), 4),
+           "p99_ms": round(float(np.percentile(ms, 99)), 4),
+           "mean_ms": round(float(ms.mean()), 4),
+           "fixed_tc256_p50_ms": round(float(np.percentile(fx, 50)), 4),
+           "fixed_tc256_p99_ms": round(float(np.percentile(fx, 99)), 4),
+           "pixels": int(sum(r["W"] * r["H"] for r in rows))}
+    # ---- all frames in one persistent launch (after their culls)
+    frs = [fr for fr, _ in frames]
+    bws = ndg.batch_workspace(len(frs), device)
+    stamps = torch.zeros(1 + len(frs), dtype=torch.int64, device=device)
+    render_batch(frs, bws, stamps)  # untimed
+    torch.cuda.synchronize()
+    tr = ndg.Trace()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    render_batch(frs, bws, stamps, trace=tr)
+    e1.record()
+    torch.cuda.synchronize()
+    st = stamps.cpu().numpy().astype(np.int64)
+    done_ms = (st[1:] - st[0]) / 1e6
+    same = all(torch.equal(fr.y, ref) for fr, ref in frames)
+    status = [ndg.read_status(fr.evaluator(256).ws) for fr in frs]
+    out["batch"] = {
+        "launches_forward": 1, "culls": len(frs),
+        "total_ms": round(e0.elapsed_time(e1), 3),
+        "forward_launch_ms": round(tr.ms(), 3),
+        "sum_one_at_a_time_tc256_ms": round(float(fx.sum()), 3),
+        "makespan_ms_device": round(float(done_ms.max()), 3),
+        "completion_p50_ms_device": round(float(np.percentile(done_ms, 50)), 3),
+        "completion_p99_ms_device": round(float(np.percentile(done_ms, 99)), 3),
+        "outputs_equal_one_at_a_time": bool(same),
+        "status_ok": all(v == ndg.NDG_OK for v in status),
+        "entries": int(sum(r["E"] for r in rows))}
+    for r, d in zip(rows, done_ms):
+        r["batch_done_ms"] = round(float(d), 3)
+    out["per_frame"] = rows
+    return out
 
 
 def run_fit_n10(device, steps: int = 5000, pool: int = 8, time_cap_s: float = 540.0) -> dict:

@@ -297,6 +297,42 @@ ndg_status ndg_densify(ndg_mixture* mix, float a_thr, float a_child0,
 ndg_status ndg_forward_noalloc(const ndg_mixture* mix, const ndg_queries* q,
                                const ndg_cull* cull, float* y, ndg_stream stream);
 
+/* One frame of a batched render: ndg_forward's arguments for that frame. */
+typedef struct ndg_frame {
+  const ndg_mixture* mix;
+  const ndg_queries* q;
+  const ndg_cull* cull; /* from ndg_build_cull on this mix and q */
+  float* y;             /* [Q][3] */
+  void* ws;             /* this frame's workspace: at least
+                           ndg_workspace_size(mix, q, NULL, 0) bytes */
+  size_t ws_bytes;
+} ndg_frame;
+
+/* Bytes of the batch descriptor workspace of ndg_forward_batch. */
+size_t ndg_batch_workspace_size(int n_frames);
+
+/* Eq. 1 and Eq. 8 for many frames (mixtures and query sets of uneven size,
+ * 1 <= N <= 12 each) in one persistent launch of the tensor-core form.  The
+ * work list is every (frame, query tile) in the order of `frames`; one CTA
+ * per SM takes the next item with an atomic cursor, so a frame's last tiles
+ * overlap the next frame's first ones.  Each frame's y equals that of
+ * ndg_forward(..., NDG_MODE_TC, ...) on the same frame, bit for bit.
+ *   frames    HOST array [n_frames] (read during the call only); frames with
+ *             Q = 0 contribute no work.
+ *   batch_ws  device, >= ndg_batch_workspace_size(n_frames) bytes, 256-byte
+ *             aligned; holds the work list (written by a host-to-device
+ *             copy issued on `stream`).
+ *   stamps    device [1 + n_frames] or NULL: %globaltimer nanoseconds;
+ *             stamps[0] the start of the first CTA, stamps[1 + f] the moment
+ *             the last tile of frame f completed (0 for an empty frame).
+ * Each frame's status (non-finite parameters, timed-out waits) goes to its
+ * own workspace (ndg_read_status on frames[f].ws).  Argument errors of any
+ * frame return NDG_ERR_INVALID_ARG (NDG_ERR_WORKSPACE for a short ws)
+ * before anything runs. */
+ndg_status ndg_forward_batch(const ndg_frame* frames, int n_frames, void* batch_ws,
+                             size_t batch_ws_bytes, unsigned long long* stamps,
+                             ndg_stream stream, ndg_trace* trace);
+
 /* Failure-detection self-test of the bounded device waits: launches one
  * CTA that waits on an mbarrier nothing ever completes, with the wait the
  * tensor-core kernels use (which = 0: the sleeping warp wait, about a

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libndg.so")
 SOURCES = ["primitives.cu", "cull.cu", "eval.cu", "train.cu", "api.cu", "noalloc.cu", "fwd_h.cu",
-           "bwd_h.cu", "bwd_hb.cu", "selftest.cu", "probe.cu"]
+           "fwd_batch.cu", "bwd_h.cu", "bwd_hb.cu", "selftest.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

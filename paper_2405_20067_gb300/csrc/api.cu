@@ -17,6 +17,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -417,6 +418,114 @@ ndg_status ndg_forward(const ndg_mixture* mix, const ndg_queries* q, const ndg_c
   }
   tr.begin();
   tr += mode == NDG_MODE_TC ? launch_fwd_tc(mix->N, fa, z.T, s) : launch_fwd(mix->N, fa, z.T, s);
+  tr.end();
+  return cuda_ok();
+}
+
+namespace {
+
+// ndg_forward_batch's descriptor workspace: the frames' forward arguments,
+// their N, the item prefix over frames, per-frame completion counters and
+// the work-list cursor (one host-to-device copy of a host image).
+struct BatchLayout {
+  size_t frames, N, tile_start, done, cursor, end;
+};
+
+BatchLayout batch_layout(int n) {
+  BatchLayout b{};
+  b.frames = 0;
+  b.N = align_up(b.frames + (size_t)n * sizeof(FwdArgs));
+  b.tile_start = align_up(b.N + (size_t)n * sizeof(int));
+  b.done = align_up(b.tile_start + (size_t)(n + 1) * sizeof(long long));
+  b.cursor = align_up(b.done + (size_t)n * sizeof(unsigned long long));
+  b.end = align_up(b.cursor + sizeof(unsigned long long));
+  return b;
+}
+
+}  // namespace
+
+size_t ndg_batch_workspace_size(int n_frames) {
+  return n_frames < 1 ? 0 : batch_layout(n_frames).end;
+}
+
+ndg_status ndg_forward_batch(const ndg_frame* frames, int n_frames, void* batch_ws,
+                             size_t batch_ws_bytes, unsigned long long* stamps,
+                             ndg_stream stream, ndg_trace* trace) {
+  if (!frames || n_frames < 1 || n_frames > (1 << 24)) return NDG_ERR_INVALID_ARG;
+  if (!batch_ws || !aligned(batch_ws, kAlign)) return NDG_ERR_INVALID_ARG;
+  if (stamps && !aligned(stamps, 8)) return NDG_ERR_INVALID_ARG;
+  const BatchLayout bl = batch_layout(n_frames);
+  if (batch_ws_bytes < bl.end) return NDG_ERR_WORKSPACE;
+  // every frame is checked before anything runs
+  for (int f = 0; f < n_frames; ++f) {
+    const ndg_frame& fr = frames[f];
+    ndg_status st;
+    if ((st = check_mix(fr.mix)) || (st = check_queries(fr.q)) || (st = check_cull(fr.cull)))
+      return st;
+    if (fr.q->Q > 0 && !fr.y) return NDG_ERR_INVALID_ARG;
+    if (!fr.ws || !aligned(fr.ws, kAlign)) return NDG_ERR_INVALID_ARG;
+    if (fr.ws_bytes < common_layout(make_sizes(fr.mix, fr.q, nullptr, 0)).end)
+      return NDG_ERR_WORKSPACE;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Tracer tr(trace, s);
+  std::vector<char> img(bl.end, 0);
+  FwdArgs* fa = reinterpret_cast<FwdArgs*>(img.data() + bl.frames);
+  int* Ns = reinterpret_cast<int*>(img.data() + bl.N);
+  long long* ts = reinterpret_cast<long long*>(img.data() + bl.tile_start);
+  long long items = 0;
+  unsigned smem = 0;
+  for (int f = 0; f < n_frames; ++f) {
+    const ndg_frame& fr = frames[f];
+    const Sizes z = make_sizes(fr.mix, fr.q, nullptr, 0);
+    const CommonLayout c = common_layout(z);
+    char* w = (char*)fr.ws;
+    PrepArgs pa = prep_args(fr.mix);
+    pa.rec = (float*)(w + c.rec);
+    pa.rec_kind = 1;  // the tensor-core form's records
+    pa.status = &reinterpret_cast<WsHeader*>(w + c.header)->status;
+    tr += launch_prep(fr.mix->N, pa, s);
+    FwdArgs& a = fa[f];
+    a.x = fr.q->x;
+    a.Q = fr.q->Q;
+    a.tile = fr.q->tile_size;
+    a.offsets = fr.cull->offsets;
+    a.ids = fr.cull->ids;
+    a.rec = pa.rec;
+    a.Ge = pa.Ge;
+    a.y = fr.y;
+    a.status = pa.status;
+    Ns[f] = fr.mix->N;
+    ts[f] = items;
+    if (fr.q->Q > 0) {
+      items += z.T;
+      const unsigned m = fwd_tc_smem(fr.mix->N);
+      smem = m > smem ? m : smem;
+    }
+  }
+  ts[n_frames] = items;
+  char* bw = (char*)batch_ws;
+  // pageable source: the copy has consumed img when the call returns
+  cudaMemcpyAsync(bw, img.data(), bl.end, cudaMemcpyHostToDevice, s);
+  if (stamps) {
+    cudaMemsetAsync(stamps, 0, sizeof(unsigned long long) * (size_t)(n_frames + 1), s);
+    cudaMemsetAsync(stamps, 0xff, sizeof(unsigned long long), s);  // start: min over CTAs
+  }
+  FwdBatchArgs b{};
+  b.frames = reinterpret_cast<const FwdArgs*>(bw + bl.frames);
+  b.N = reinterpret_cast<const int*>(bw + bl.N);
+  b.tile_start = reinterpret_cast<const long long*>(bw + bl.tile_start);
+  b.done = reinterpret_cast<unsigned long long*>(bw + bl.done);
+  b.cursor = reinterpret_cast<unsigned long long*>(bw + bl.cursor);
+  b.stamps = stamps;
+  b.n_frames = n_frames;
+  b.n_items = items;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)(items < (long long)sms ? items : (long long)sms);
+  tr.begin();
+  tr += launch_fwd_tc_batch(b, smem, grid, s);
   tr.end();
   return cuda_ok();
 }

@@ -58,6 +58,20 @@ struct FwdArgs {
   const int* n_tiles;
 };
 
+// Many frames' tensor-core forwards in one persistent launch: the work list
+// is every (frame, tile) item in frame order, taken with an atomic cursor.
+struct FwdBatchArgs {
+  const FwdArgs* frames;         // [n_frames] (tiles / n_tiles unused)
+  const int* N;                  // [n_frames]
+  const long long* tile_start;   // [n_frames + 1]: frame f owns items tile_start[f] ..
+  unsigned long long* done;      // [n_frames] tiles completed (zero before the launch)
+  unsigned long long* cursor;    // next item (zero before the launch)
+  unsigned long long* stamps;    // [1 + n_frames] %globaltimer ns, or null: [0] first CTA
+                                 // start (~0 before the launch), [1 + f] frame f complete
+  int n_frames;
+  long long n_items;
+};
+
 struct BwdArgs {
   const float* x;
   const float* dy;
@@ -126,6 +140,8 @@ int launch_tile_split(const long long* offsets, long long T, long long min_cand,
                       int* n_a, int* n_b, cudaStream_t s);
 int launch_fwd(int N, const FwdArgs& a, long long T, cudaStream_t s);
 int launch_fwd_tc(int N, const FwdArgs& a, long long T, cudaStream_t s);  // FP16 hi/lo, N <= 12
+unsigned fwd_tc_smem(int N);  // dynamic shared memory of the tensor-core forward for N (0: none)
+int launch_fwd_tc_batch(const FwdBatchArgs& b, unsigned smem, int grid, cudaStream_t s);
 int launch_bwd_h(int N, const BwdArgs& a, long long T, cudaStream_t s);   // N <= 6
 int launch_bwd_hb(int N, const BwdArgs& a, long long T, cudaStream_t s);  // beta form, N <= 12
 // n outputs; norm: the count the loss is normalised by (0: n)

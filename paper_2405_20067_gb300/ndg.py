@@ -68,6 +68,11 @@ class CullC(ctypes.Structure):
     _fields_ = [("offsets", _P), ("ids", _P), ("E_cap", ctypes.c_longlong), ("E_dev", _P)]
 
 
+class FrameC(ctypes.Structure):
+    _fields_ = [("mix", ctypes.POINTER(MixtureC)), ("q", ctypes.POINTER(QueriesC)),
+                ("cull", ctypes.POINTER(CullC)), ("y", _P), ("ws", _P), ("ws_bytes", ctypes.c_size_t)]
+
+
 class TraceC(ctypes.Structure):
     _fields_ = [("main_begin", _P), ("main_end", _P), ("launches", ctypes.c_longlong)]
 
@@ -102,7 +107,8 @@ def _tr(trace):
 EXPORTS = ["ndg_workspace_size", "ndg_build_cull", "ndg_build_cull_conditioned", "ndg_forward",
            "ndg_loss_l2", "ndg_loss_rel_l2", "ndg_backward", "ndg_adam", "ndg_densify",
            "ndg_read_status", "ndg_status_string", "ndg_version", "ndg_forward_noalloc",
-           "ndg_selftest_timeout", "ndg_probe_pipe", "ndg_loss_l2_shard"]
+           "ndg_selftest_timeout", "ndg_probe_pipe", "ndg_loss_l2_shard",
+           "ndg_batch_workspace_size", "ndg_forward_batch"]
 NDG_ERR_SCRATCH_LIMIT = 7
 
 
@@ -133,6 +139,9 @@ def lib():
                                ctypes.c_float, _P, TR]
         L.ndg_densify.argtypes = [M, ctypes.c_float, ctypes.c_float, _P, M, M, _P, _P, sz, _P, TR]
         L.ndg_forward_noalloc.argtypes = [M, Qp, C, _P, _P]
+        L.ndg_batch_workspace_size.argtypes = [ctypes.c_int]
+        L.ndg_batch_workspace_size.restype = sz
+        L.ndg_forward_batch.argtypes = [ctypes.POINTER(FrameC), ctypes.c_int, _P, sz, _P, _P, TR]
         L.ndg_selftest_timeout.argtypes = [ctypes.c_int, _P, sz, _P]
         L.ndg_probe_pipe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
                                      _P, _P]
@@ -143,7 +152,7 @@ def lib():
         for name in ["ndg_build_cull", "ndg_build_cull_conditioned", "ndg_forward", "ndg_loss_l2",
                      "ndg_loss_rel_l2", "ndg_backward", "ndg_adam", "ndg_densify",
                      "ndg_read_status", "ndg_forward_noalloc", "ndg_selftest_timeout",
-                     "ndg_probe_pipe", "ndg_loss_l2_shard"]:
+                     "ndg_probe_pipe", "ndg_loss_l2_shard", "ndg_forward_batch"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -328,6 +337,29 @@ def forward_noalloc(mix: Mixture, x: torch.Tensor, tile: int, cull: Cull, y: tor
     _check(lib().ndg_forward_noalloc(ctypes.byref(mix.c()), ctypes.byref(queries_c(x, tile)),
                                      ctypes.byref(cull.c()), _ptr(y), _stream(stream)),
            "ndg_forward_noalloc")
+
+
+def batch_workspace(n_frames: int, device="cuda") -> torch.Tensor:
+    """The descriptor workspace of forward_batch for n_frames frames."""
+    return workspace(int(lib().ndg_batch_workspace_size(int(n_frames))), device)
+
+
+def forward_batch(frames, batch_ws: torch.Tensor, stamps: torch.Tensor | None = None,
+                  stream=None, trace: Trace | None = None):
+    """ndg_forward_batch: the tensor-core forward of many frames in one
+    persistent launch.  frames: sequence of (mix, x, tile, cull, y, ws), each
+    as for forward(); stamps: int64 [1 + len(frames)] on the device or None
+    (%globaltimer ns: [0] launch start, [1 + f] frame f complete)."""
+    keep = []
+    arr = (FrameC * len(frames))()
+    for i, (mix, x, tile, cull, y, ws) in enumerate(frames):
+        mc, qc, cc = mix.c(), queries_c(x, tile), cull.c()
+        keep += [mc, qc, cc]
+        arr[i] = FrameC(ctypes.pointer(mc), ctypes.pointer(qc), ctypes.pointer(cc),
+                        y.data_ptr(), ws.data_ptr(), ws.numel())
+    _check(lib().ndg_forward_batch(arr, len(frames), _ptr(batch_ws), batch_ws.numel(),
+                                   _ptr(stamps) if stamps is not None else None,
+                                   _stream(stream), _tr(trace)), "ndg_forward_batch")
 
 
 def loss_l2(y: torch.Tensor, target: torch.Tensor, dy: torch.Tensor, loss: torch.Tensor,

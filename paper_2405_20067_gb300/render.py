@@ -6,8 +6,13 @@ launch configuration of a frame -- the evaluation form (tensor cores, the
 per-tile automatic choice, or FP32) and the query-tile size (256 or 128
 queries: 16 x 16 or 16 x 8 pixels) -- is picked by `Autotuner`: the first
 frame of each class (N, G rounded to a power of two, pixel count rounded to
-a power of two) is rendered once with every candidate configuration, the
-fastest is kept for the class, and later frames of the class reuse it.
+a power of two) is rendered `reps` times with every candidate configuration,
+the configuration with the lowest median time is kept for the class, and
+later frames of the class reuse it.
+
+`render_batch` renders many frames with one persistent launch of the
+tensor-core forward (ndg_forward_batch) after their culls, and returns the
+device's per-frame completion stamps.
 """
 from __future__ import annotations
 
@@ -31,15 +36,22 @@ def frame_class(N: int, G: int, Q: int) -> tuple:
 @dataclass
 class Autotuner:
     candidates: tuple = CANDIDATES
+    reps: int = 5
     cache: dict = field(default_factory=dict)
     trials: dict = field(default_factory=dict)
 
     def choose(self, key: tuple, time_config) -> tuple:
-        """time_config(cfg) -> ms of one frame; tried once per class."""
+        """time_config(cfg) -> ms of one frame; each candidate is timed
+        `reps` times (interleaved, so that drifts hit every candidate alike)
+        on the first frame of a class, and the lowest median wins."""
         if key not in self.cache:
-            times = {cfg: time_config(cfg) for cfg in self.candidates}
-            self.trials[key] = times
-            self.cache[key] = min(times, key=times.get)
+            samples = {cfg: [] for cfg in self.candidates}
+            for _ in range(self.reps):
+                for cfg in self.candidates:
+                    samples[cfg].append(time_config(cfg))
+            med = {cfg: sorted(v)[len(v) // 2] for cfg, v in samples.items()}
+            self.trials[key] = samples
+            self.cache[key] = min(med, key=med.get)
         return self.cache[key]
 
 
@@ -82,3 +94,18 @@ class Frame:
 
     def release(self):
         self._ev.clear()
+
+
+def render_batch(frames, batch_ws: torch.Tensor, stamps: torch.Tensor | None = None,
+                 tile: int = 256, trace: ndg.Trace | None = None):
+    """Culls every frame (its own launches, in order), then evaluates all of
+    them with one persistent tensor-core launch (ndg_forward_batch, work list
+    in frame order).  stamps: int64 [1 + len(frames)] on the device or None
+    (%globaltimer ns: launch start, then each frame's completion).  No
+    synchronisation; each frame's output is frame.y."""
+    items = []
+    for fr in frames:
+        ev = fr.evaluator(tile)
+        ndg.build_cull(fr.mix, fr.x, tile, fr.cp, ev.cull, ev.ws)
+        items.append((fr.mix, fr.x, tile, ev.cull, fr.y, ev.ws))
+    ndg.forward_batch(items, batch_ws, stamps, trace=trace)

@@ -150,3 +150,39 @@ def test_noalloc_rejects_bad_pointers_on_host(ndg):
     big = ndg.MixtureC(6, 200_000, 200_000, 0, fake, fake, fake, fake, None, None, None, None)
     assert L.ndg_forward_noalloc(ctypes.byref(big), ctypes.byref(q), ctypes.byref(cull), y,
                                  None) == ndg.NDG_ERR_SCRATCH_LIMIT
+
+
+def test_forward_batch_host_checks(ndg):
+    """ndg_forward_batch sizes its descriptor workspace and rejects bad
+    arguments of any frame before any CUDA call."""
+    L = ndg.lib()
+    assert L.ndg_batch_workspace_size(0) == 0
+    s1, s64 = L.ndg_batch_workspace_size(1), L.ndg_batch_workspace_size(64)
+    assert 0 < s1 < s64 and s64 % 256 == 0
+    m = _mix_c(ndg)
+    q = ndg.QueriesC(1000, 256, ctypes.c_void_p(0x2000))
+    c = ndg.CullC(ctypes.c_void_p(0x4000), ctypes.c_void_p(0x5000), 100, ctypes.c_void_p(0x6000))
+    fake_ws = ctypes.c_void_p(0x10000)
+
+    def frames(*fs):
+        arr = (ndg.FrameC * len(fs))()
+        for i, (mm, y, ws, nb) in enumerate(fs):
+            arr[i] = ndg.FrameC(ctypes.pointer(mm), ctypes.pointer(q), ctypes.pointer(c), y, ws, nb)
+        return arr
+
+    good = (m, 0x7000, 0x10000, 1 << 30)
+    bad_n = _mix_c(ndg, N=13)
+    E = ndg.NDG_ERR_INVALID_ARG
+    # no frames, no descriptor workspace, misaligned descriptor workspace
+    assert L.ndg_forward_batch(frames(good), 0, fake_ws, s1, None, None, None) == E
+    assert L.ndg_forward_batch(frames(good), 1, None, s1, None, None, None) == E
+    assert L.ndg_forward_batch(frames(good), 1, ctypes.c_void_p(0x10010), s1, None, None, None) == E
+    # descriptor workspace too small
+    assert L.ndg_forward_batch(frames(good, good), 2, fake_ws, s1 - 256, None, None,
+                               None) == ndg.NDG_ERR_WORKSPACE
+    # a bad second frame: N out of range, no output, misaligned or short workspace
+    for f2 in [(bad_n, 0x7000, 0x10000, 1 << 30), (m, None, 0x10000, 1 << 30),
+               (m, 0x7000, 0x10008, 1 << 30)]:
+        assert L.ndg_forward_batch(frames(good, f2), 2, fake_ws, s64, None, None, None) == E
+    assert L.ndg_forward_batch(frames(good, (m, 0x7000, 0x10000, 16)), 2, fake_ws, s64, None,
+                               None, None) == ndg.NDG_ERR_WORKSPACE
