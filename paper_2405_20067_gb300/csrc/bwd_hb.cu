@@ -75,6 +75,9 @@ struct BwdBShape {
   static constexpr int NPART = N <= 8 ? 2 : 4;  // the record is formed in parts
   static constexpr int PARTW = (RPT / NPART + 3) / 4 * 4;
   static constexpr int PQMAX = PARTW / 4;
+  // staging row stride in float4s: odd, so that 8 consecutive rows' 16-byte
+  // stores fall in distinct banks
+  static constexpr int PQS = PQMAX | 1;
   // Phi: per 8-query group, hi cores (KP / 8 x 128 B) then lo cores
   static constexpr uint32_t GRP = 2u * KP * 16;         // bytes per 8-query group
   static constexpr uint32_t LO_OFF = (uint32_t)KP * 16;  // lo cores inside a group
@@ -82,13 +85,14 @@ struct BwdBShape {
   static constexpr uint32_t SBO_C = (KP / 8) * 128;      // coefficient rows: 8-row groups
   static constexpr uint32_t C_BYTES = (uint32_t)NC * KP * 2;
   static constexpr uint32_t C_STAGE = 2 * C_BYTES;       // hi, lo
-  // stash slot: per candidate m~ (N), w / rho (3), entry, row factor, rho;
-  // then the two column halves' sum_q e dy' (float4 each)
+  // stash slot: SV fields per candidate, field-major ([SV][NC]: lane j
+  // reads word j of a field, conflict-free): m~ (N), w / rho (3), entry,
+  // row factor, rho; then the two column halves' sum_q e dy' (float4 each)
   static constexpr int SV = (N + 6 + 3) / 4 * 4;
   static constexpr uint32_t SLOT = (uint32_t)NC * SV * 4 + 2u * NC * 16;
   static constexpr int SS = N >= 9 ? 3 : 4;  // >= 3: the chain runs one chunk behind the epilogue
   static constexpr uint32_t DYC = 3u * 256 * 4;  // dy' by colour
-  static constexpr uint32_t OUT_BYTES = 16u * (PQMAX + 1) * 16;
+  static constexpr uint32_t OUT_BYTES = 16u * PQS * 16;
   static constexpr uint32_t FIXED = PHI_BYTES + SS * SLOT + DYC + 8 * OUT_BYTES + 128 + 4096;
   // coefficient stages: as many as fit (up to 3; N = 12 has room for one)
   static constexpr int CS = FIXED + 3 * C_STAGE <= 227u * 1024u   ? 3
@@ -383,7 +387,7 @@ __global__ void __launch_bounds__(416, 1) bwd_hb_kernel(BwdArgs a) {
       const uint32_t wexp = (__float_as_uint(wm) >> 23) & 0xffu;
       const float rho = (wexp >= 1u && wexp <= 253u) ? __uint_as_float((wexp + 1u) << 23) : 1.0f;
       const float irho = 1.0f / rho;  // exact: a power of two
-      float sv[SV];
+      float sv[N + 6];
 #pragma unroll
       for (int d = 0; d < N; ++d) sv[d] = mt[d];
 #pragma unroll
@@ -391,12 +395,9 @@ __global__ void __launch_bounds__(416, 1) bwd_hb_kernel(BwdArgs a) {
       sv[N + 3] = __int_as_float(slot);
       sv[N + 4] = back;
       sv[N + 5] = rho;
+      float* dst = slot_f(i) + j;
 #pragma unroll
-      for (int k = N + 6; k < SV; ++k) sv[k] = 0.0f;
-      float4* dst = reinterpret_cast<float4*>(slot_f(i) + j * SV);
-#pragma unroll
-      for (int k = 0; k < SV / 4; ++k)
-        dst[k] = make_float4(sv[4 * k], sv[4 * k + 1], sv[4 * k + 2], sv[4 * k + 3]);
+      for (int k = 0; k < N + 6; ++k) dst[k * NC] = sv[k];
       warp_arrive(&stash_full[i % SS]);
       return true;
     };
@@ -507,7 +508,7 @@ __global__ void __launch_bounds__(416, 1) bwd_hb_kernel(BwdArgs a) {
     // (hi + lo blocks summed), dl/dw_c = dys (sum of the two halves' e dy').
     // the chain's per-candidate stash row and sum_q e dy' (captured, so that
     // they stay in registers)
-    float sv[SV], gw[3];
+    float sv[N + 6], gw[3];
     auto part = [&](int ic, auto gtag) {
       constexpr int GG = decltype(gtag)::value;
       constexpr int p0 = GG * S::PARTW;
@@ -602,7 +603,7 @@ __global__ void __launch_bounds__(416, 1) bwd_hb_kernel(BwdArgs a) {
       // store coalesced; entries past the tile's end are not written
       const long long w0 = beg + (long long)ic * NC + quad * 32;
       const long long nval = end - w0 < 32 ? end - w0 : 32;
-      float4* stg = Outs + (warp - 4) * (16 * (S::PQMAX + 1));
+      float4* stg = Outs + (warp - 4) * (16 * S::PQS);
       float4* dst = reinterpret_cast<float4*>(a.part) + w0 * S::RQT + p0 / 4;
 #pragma unroll
       for (int hb = 0; hb < 2; ++hb) {
@@ -610,7 +611,7 @@ __global__ void __launch_bounds__(416, 1) bwd_hb_kernel(BwdArgs a) {
           const int r = lane & 15;
 #pragma unroll
           for (int k = 0; k < PQ; ++k)
-            stg[r * (S::PQMAX + 1) + k] =
+            stg[r * S::PQS + k] =
                 make_float4(val[4 * k], val[4 * k + 1], val[4 * k + 2], val[4 * k + 3]);
         }
         __syncwarp();
@@ -619,7 +620,7 @@ __global__ void __launch_bounds__(416, 1) bwd_hb_kernel(BwdArgs a) {
         for (int m = 0; m < (16 * PQ + 31) / 32; ++m) {
           const int idx = m * 32 + lane;
           const int r = idx / PQ, k = idx - r * PQ;
-          if (r < nrec) dst[(long long)(16 * hb + r) * S::RQT + k] = stg[r * (S::PQMAX + 1) + k];
+          if (r < nrec) dst[(long long)(16 * hb + r) * S::RQT + k] = stg[r * S::PQS + k];
         }
         __syncwarp();
       }
@@ -629,12 +630,8 @@ __global__ void __launch_bounds__(416, 1) bwd_hb_kernel(BwdArgs a) {
       if (!warp_wait(&gw_full[ic % SS], (ic / SS) & 1, abort_flag)) return false;
       {
         const float* sl = slot_f(ic);
-        const float4* stp = reinterpret_cast<const float4*>(sl + j * SV);
 #pragma unroll
-        for (int k = 0; k < SV / 4; ++k) {
-          const float4 v = stp[k];
-          sv[4 * k] = v.x; sv[4 * k + 1] = v.y; sv[4 * k + 2] = v.z; sv[4 * k + 3] = v.w;
-        }
+        for (int k = 0; k < N + 6; ++k) sv[k] = sl[k * NC + j];
         const float4* g2 = reinterpret_cast<const float4*>(sl + NC * SV);
         const float4 ga = g2[j], gb = g2[NC + j];
         gw[0] = ga.x + gb.x;
@@ -671,11 +668,11 @@ __global__ void __launch_bounds__(416, 1) bwd_hb_kernel(BwdArgs a) {
       if (!ok) break;
       fence_after_sync();
       if (h == 0) {
-        const float* st = slot_f(i) + j * SV;
-        w0 = st[N];
-        w1 = st[N + 1];
-        w2 = st[N + 2];
-        back = st[N + 4];
+        const float* st = slot_f(i) + j;
+        w0 = st[N * NC];
+        w1 = st[(N + 1) * NC];
+        w2 = st[(N + 2) * NC];
+        back = st[(N + 4) * NC];
         g0 = g1 = g2 = make_float2(0.f, 0.f);
       }
       constexpr int WC = S::UQ / 2;
