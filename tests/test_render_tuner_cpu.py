@@ -22,7 +22,7 @@ def test_autotuner_times_each_candidate_reps_times_per_class():
     assert t.choose((6, 13, 16), timer) == ("auto", 256)
     assert len(calls) == t.reps * len(CANDIDATES)
     assert sorted(set(calls)) == sorted(CANDIDATES)
-    # interleaved: every round times each candidate once
+    # interleaved: every pass times each candidate once
     assert calls[:len(CANDIDATES)] == list(CANDIDATES)
     calls.clear()
     assert t.choose((6, 13, 16), timer) == ("auto", 256)  # cached
