@@ -618,6 +618,38 @@ def run_render_batch(device, n_frames: int = 64) -> dict:
     return out
 
 
+def run_frame_fwd_bwd(device, N: int, G: int, W: int, H: int, steps: int) -> dict:
+    """One frame (W x H surface queries, 16 x 16 pixel tiles) against G
+    N-dimensional Gaussians: cull once, then `steps` tensor-core forwards and
+    backwards (dy fixed), each timed with CUDA events; a small, seeded case
+    for profiling the evaluation kernels (S4, S5, S7)."""
+    import torch
+    from paper_2405_20067_gb300 import ndg, synth
+    gm = ndg.Mixture.from_arrays(N, synth.mixture(N, G, 21), device=device)
+    x = torch.as_tensor(synth.queries_frame(N, W, H, 22)).to(device)
+    cp = ndg.CullParams(K_PROJ, torch.as_tensor(synth.projections(N, K_PROJ, 23)).to(device),
+                        CUTOFF, 3.0, BUCKETS)
+    ev = ndg.Evaluator(gm, x, TILE, cp)
+    E = ev.build(gm)
+    dy = torch.as_tensor((synth.rng(24).standard_normal((x.shape[0], 3)) / x.shape[0])
+                         .astype("float32")).to(device)
+    fwd, bwd = [], []
+    for _ in range(steps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        ev.forward(gm, mode=ndg.NDG_MODE_TC)
+        e1.record()
+        ev.backward(gm, dy, mode=ndg.NDG_MODE_TC)
+        e2.record()
+        torch.cuda.synchronize()
+        fwd.append(e0.elapsed_time(e1))
+        bwd.append(e1.elapsed_time(e2))
+    assert ndg.read_status(ev.ws) == ndg.NDG_OK
+    return {"workload": f"N={N} {W}x{H} frame, {G} Gaussians, tile {TILE}, k={K_PROJ}, "
+                        "cutoff 1/255", "entries": int(E), "pairs": int(E) * TILE,
+            "forward_ms": [round(v, 4) for v in fwd], "backward_call_ms": [round(v, 4) for v in bwd]}
+
+
 def run_fit_n10(device, steps: int = 5000, pool: int = 8, time_cap_s: float = 540.0) -> dict:
     """The N = 10 fit (config 3 shape): a synthetic ground truth of 2M
     Gaussians drawn as the 10-D recipe, a fitted mixture of 50k parents
@@ -708,6 +740,9 @@ def main():
     ap.add_argument("--fit-n10", action="store_true",
                     help="only the N = 10 fit with refinement (loss curve, G(t), wall time); "
                          "one JSON line")
+    ap.add_argument("--frame-fwd-bwd", metavar="N,G,WxH", default=None,
+                    help="only tensor-core forwards and backwards of one seeded frame (e.g. "
+                         "10,5000,960x544: a small case for profiling); one JSON line")
     ap.add_argument("--ablation", action="store_true",
                     help="only the culling ablations (k_sigma sweep, culling on / off); one "
                          "JSON line")
@@ -738,6 +773,13 @@ def main():
         if rank == 0:
             print(json.dumps({"render": render_n10_1080p(device, max(3, args.steps // 4), args.warmup,
                                                          flush, res=(w_, h_))}))
+        return
+    if args.frame_fwd_bwd:
+        n_, g_, wh = args.frame_fwd_bwd.split(",")
+        w_, h_ = (int(v) for v in wh.lower().split("x"))
+        if rank == 0:
+            print(json.dumps({"frame_fwd_bwd": run_frame_fwd_bwd(device, int(n_), int(g_), w_, h_,
+                                                                 args.steps)}))
         return
     if args.fit_n10:
         if rank == 0:
