@@ -22,8 +22,11 @@
  *     (capacity overflow, non-finite parameters) are written to a status
  *     word inside the workspace and read with ndg_read_status().
  *   - `ws` is scratch device memory of at least ndg_workspace_size() bytes
- *     (256-byte aligned).  Calls that share a workspace must be ordered on
- *     one stream.
+ *     (256-byte aligned).  Calls that share a workspace must be ordered (one
+ *     stream, or events between streams), with one exception:
+ *     ndg_backward_order writes only the backward's part of the workspace
+ *     and may run concurrently with ndg_forward and the loss calls (not with
+ *     ndg_build_cull, ndg_backward or ndg_densify).
  *   - Raw parameters (per parent row g, G rows in use, G_cap allocated):
  *       mean      [G_cap][N]
  *       theta     [G_cap][P]  P = N(N+1)/2, packed lower triangle row by
@@ -227,6 +230,25 @@ ndg_status ndg_loss_rel_l2(long long Q, const float* y, const float* target,
                            float eps, float* dy, double* loss_dev, void* ws,
                            size_t ws_bytes, ndg_stream stream, ndg_trace* trace);
 
+/* The Gaussian-major order of `cull`'s entries that ndg_backward sums the
+ * per-entry gradient records in (a stable transposition of the candidate
+ * lists: per Gaussian, its entries in tile order), written into the
+ * backward's part of `ws` (same size rule as ndg_backward).  It depends on
+ * the lists only, so it can run on another stream while the forward and the
+ * loss run; ndg_backward with mode | NDG_BWD_ORDER_READY then uses it
+ * instead of recomputing it.  The caller orders the two calls (an event)
+ * and passes the same mix sizes, q, cull and ws to both.  Same argument
+ * errors as ndg_backward's. */
+ndg_status ndg_backward_order(const ndg_mixture* mix, const ndg_queries* q, const ndg_cull* cull,
+                              void* ws, size_t ws_bytes, ndg_stream stream, ndg_trace* trace);
+
+/* Flag for ndg_backward's mode: the order of ndg_backward_order is already
+ * in ws for this cull.  An order left from other lists cannot make the
+ * backward read outside the workspace (indices are bounds-checked, and an
+ * index out of range sets NDG_ERR_INVALID_ARG in the status word), but its
+ * gradients are then wrong. */
+#define NDG_BWD_ORDER_READY 0x100
+
 /* Analytic gradient of the loss through Eq. 1, 2, 6-8 given dy = dl/dy
  * [Q][3]: writes dl/d(raw parameter) into `grad` (same layout and N, G,
  * has_children as mix; rows >= G untouched).  Recomputes everything from
@@ -236,8 +258,9 @@ ndg_status ndg_loss_rel_l2(long long Q, const float* y, const float* target,
  * lifted form on the tensor cores, every N (for N <= 6 the gradients of the
  * lifted coefficients and of w come from a second contraction E Psi with
  * Psi = dy (x) phi; above, from beta Phi with beta = e sum_c dy_c w_c and
- * dl/dw summed in FP32); NDG_MODE_AUTO: NDG_MODE_TC.  Tensor-core gradients
- * are within ~3e-4 relative of the FP64 definition per tensor. */
+ * dl/dw summed in FP32); NDG_MODE_AUTO: NDG_MODE_TC; any of them may carry
+ * NDG_BWD_ORDER_READY.  Tensor-core gradients are within ~6e-4 relative of
+ * the FP64 definition per tensor. */
 ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q,
                         const ndg_cull* cull, int mode, const float* dy,
                         ndg_mixture* grad, void* ws, size_t ws_bytes,

@@ -584,23 +584,81 @@ ndg_status ndg_selftest_timeout(int which, void* ws, size_t ws_bytes, ndg_stream
   return cuda_ok();
 }
 
+namespace {
+
+// Gaussian-major order of the entries (the stable order of a sort by
+// Gaussian index): the per-entry partial records are written in entry order
+// and summed per Gaussian through this permutation.  A Gaussian occurs at
+// most once per tile, so segments are at most T long: a counting sort with
+// per-segment ranks by tile when T fits, else a radix sort.  launch = false
+// only returns where the permutation is (the buffer depends on sizes alone).
+int backward_order(const Sizes& z, const BwdLayout& L, const ndg_cull* cull, int Ge, char* w,
+                   bool launch, cudaStream_t s, int32_t** sv_out) {
+  long long* goff = (long long*)(w + L.goff);
+  if (z.T <= kMaxSegSort) {
+    *sv_out = (int32_t*)(w + L.sv_a);
+    if (!launch) return 0;
+    return transpose_entries(cull->ids, cull->offsets, z.T, cull->E_cap, cull->E_dev, Ge, goff,
+                             (unsigned long long*)(w + L.te), *sv_out, w + L.tmp, s);
+  }
+  const int bits = bits_for(Ge > 0 ? Ge : 1);
+  const int passes = bits < 1 ? 1 : (bits + 7) / 8;  // radix_sort_pairs: 8 bits a pass
+  if (!launch) {
+    *sv_out = (int32_t*)(w + ((passes & 1) ? L.sv_b : L.sv_a));
+    return 0;
+  }
+  uint32_t* sk;
+  int n = radix_sort_pairs((const uint32_t*)cull->ids, nullptr, (uint32_t*)(w + L.sk_a),
+                           (int32_t*)(w + L.sv_a), (uint32_t*)(w + L.sk_b), (int32_t*)(w + L.sv_b),
+                           cull->E_cap, cull->E_dev, bits, w + L.tmp, s, &sk, sv_out);
+  n += bin_boundaries(sk, cull->E_cap, cull->E_dev, Ge, goff, s);
+  return n;
+}
+
+ndg_status check_backward_args(const ndg_mixture* mix, const ndg_queries* q, const ndg_cull* cull,
+                               void* ws, size_t ws_bytes) {
+  ndg_status st;
+  if ((st = check_mix(mix)) || (st = check_queries(q)) || (st = check_cull(cull))) return st;
+  if (cull->E_cap >= (1ll << 31)) return NDG_ERR_INVALID_ARG;
+  if (!ws || !aligned(ws, kAlign)) return NDG_ERR_INVALID_ARG;
+  const Sizes z = make_sizes(mix, q, nullptr, cull->E_cap);
+  if (ws_bytes < bwd_layout(z, common_layout(z).end).end) return NDG_ERR_WORKSPACE;
+  return NDG_OK;
+}
+
+}  // namespace
+
+ndg_status ndg_backward_order(const ndg_mixture* mix, const ndg_queries* q, const ndg_cull* cull,
+                              void* ws, size_t ws_bytes, ndg_stream stream, ndg_trace* trace) {
+  ndg_status st;
+  if ((st = check_backward_args(mix, q, cull, ws, ws_bytes))) return st;
+  const Sizes z = make_sizes(mix, q, nullptr, cull->E_cap);
+  const BwdLayout L = bwd_layout(z, common_layout(z).end);
+  cudaStream_t s = (cudaStream_t)stream;
+  Tracer tr(trace, s);
+  int32_t* sv;
+  tr.begin();
+  tr += backward_order(z, L, cull, prep_args(mix).Ge, (char*)ws, true, s, &sv);
+  tr.end();
+  return cuda_ok();
+}
+
 ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q, const ndg_cull* cull,
                         int mode, const float* dy, ndg_mixture* grad, void* ws, size_t ws_bytes,
                         ndg_stream stream, ndg_trace* trace) {
   ndg_status st;
-  if ((st = check_mix(mix)) || (st = check_queries(q)) || (st = check_cull(cull))) return st;
+  const bool order_ready = (mode & NDG_BWD_ORDER_READY) != 0;
+  mode &= ~NDG_BWD_ORDER_READY;
+  if ((st = check_backward_args(mix, q, cull, ws, ws_bytes))) return st;
   if (mode == NDG_MODE_AUTO) mode = NDG_MODE_TC;
   if (mode != NDG_MODE_FP32 && mode != NDG_MODE_TC) return NDG_ERR_INVALID_ARG;
   if (!grad || grad->N != mix->N || grad->G != mix->G || grad->has_children != mix->has_children ||
       (st = check_mix(grad)))
     return st ? st : NDG_ERR_INVALID_ARG;
   if (q->Q > 0 && !dy) return NDG_ERR_INVALID_ARG;
-  if (cull->E_cap >= (1ll << 31)) return NDG_ERR_INVALID_ARG;
-  if (!ws || !aligned(ws, kAlign)) return NDG_ERR_INVALID_ARG;
   Sizes z = make_sizes(mix, q, nullptr, cull->E_cap);
   CommonLayout c = common_layout(z);
   BwdLayout L = bwd_layout(z, c.end);
-  if (ws_bytes < L.end) return NDG_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
   Tracer tr(trace, s);
   char* w = (char*)ws;
@@ -610,26 +668,10 @@ ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q, const ndg_
   pa.rec_kind = mode == NDG_MODE_TC ? 2 : 0;
   pa.status = &reinterpret_cast<WsHeader*>(w + c.header)->status;
   tr += launch_prep(N, pa, s);
-  // Gaussian-major order of the entries (the stable order of a sort by
-  // Gaussian index): the per-entry partial records are written in entry
-  // order and summed per Gaussian through this permutation.  A Gaussian
-  // occurs at most once per tile, so segments are at most T long: a counting
-  // sort with per-segment sorts in shared memory when T fits, else a radix sort.
   const int Ge = pa.Ge;
   int32_t* sv;
   long long* goff = (long long*)(w + L.goff);
-  if (z.T <= kMaxSegSort) {
-    sv = (int32_t*)(w + L.sv_a);
-    tr += transpose_entries(cull->ids, cull->offsets, z.T, cull->E_cap, cull->E_dev, Ge, goff,
-                            (unsigned long long*)(w + L.te), sv, w + L.tmp, s);
-  } else {
-    uint32_t* sk;
-    tr += radix_sort_pairs((const uint32_t*)cull->ids, nullptr, (uint32_t*)(w + L.sk_a),
-                           (int32_t*)(w + L.sv_a), (uint32_t*)(w + L.sk_b), (int32_t*)(w + L.sv_b),
-                           cull->E_cap, cull->E_dev, bits_for(Ge > 0 ? Ge : 1), w + L.tmp, s, &sk,
-                           &sv);
-    tr += bin_boundaries(sk, cull->E_cap, cull->E_dev, Ge, goff, s);
-  }
+  tr += backward_order(z, L, cull, Ge, w, !order_ready, s, &sv);
   BwdArgs ba{};
   ba.x = q->x;
   ba.dy = dy;
@@ -649,7 +691,7 @@ ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q, const ndg_
                             : launch_bwd(N, ba, z.T, s);
   tr.end();
   float* gsum = (float*)(w + L.gsum);
-  tr += launch_segsum(ba.part, part_floats(N), goff, Ge, sv, gsum, s);
+  tr += launch_segsum(ba.part, part_floats(N), goff, Ge, sv, cull->E_cap, pa.status, gsum, s);
   ChainArgs ch{};
   ch.G = mix->G;
   ch.has_children = mix->has_children;

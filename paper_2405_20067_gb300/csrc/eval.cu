@@ -380,6 +380,7 @@ __global__ void __launch_bounds__(128) bwd_kernel(BwdArgs a) {
 __global__ void __launch_bounds__(256) segsum_kernel(const float* __restrict__ part, int RP,
                                                      const long long* __restrict__ goff, int Ge,
                                                      const int32_t* __restrict__ perm,
+                                                     long long n_cap, int* status,
                                                      float* __restrict__ gsum) {
   __shared__ float4 sh[8][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -389,17 +390,29 @@ __global__ void __launch_bounds__(256) segsum_kernel(const float* __restrict__ p
   const int grp = lane / RP4, col = lane - grp * RP4;
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   if (e < Ge && grp < G && col < RP4) {
-    const long long b = goff[e], en = goff[e + 1];
+    // segment bounds and entry indices are kept inside the n_cap records
+    // (an order computed for other lists reads no foreign memory)
+    long long b = goff[e], en = goff[e + 1];
+    b = b < 0 ? 0 : (b > n_cap ? n_cap : b);
+    en = en < b ? b : (en > n_cap ? n_cap : en);
     const float4* src = reinterpret_cast<const float4*>(part);
+    bool bad = false;
     // four records of the group in flight at a time, added in entry order
     long long j = b + grp;
     for (; j + 3 * G < en; j += 4 * G) {
       long long r[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) r[u] = perm ? (long long)__ldg(perm + j + u * G) : j + u * G;
+      for (int u = 0; u < 4; ++u) {
+        r[u] = perm ? (long long)__ldg(perm + j + u * G) : j + u * G;
+        if ((unsigned long long)r[u] >= (unsigned long long)n_cap) {
+          bad = true;
+          r[u] = -1;
+        }
+      }
       float4 v[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = __ldg(src + r[u] * RP4 + col);
+      for (int u = 0; u < 4; ++u)
+        v[u] = r[u] >= 0 ? __ldg(src + r[u] * RP4 + col) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         acc.x += v[u].x; acc.y += v[u].y; acc.z += v[u].z; acc.w += v[u].w;
@@ -407,9 +420,14 @@ __global__ void __launch_bounds__(256) segsum_kernel(const float* __restrict__ p
     }
     for (; j < en; j += G) {
       const long long r = perm ? (long long)__ldg(perm + j) : j;
+      if ((unsigned long long)r >= (unsigned long long)n_cap) {
+        bad = true;
+        continue;
+      }
       const float4 v = __ldg(src + r * RP4 + col);
       acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
     }
+    if (bad && status) set_status(status, NDG_ERR_INVALID_ARG);
   }
   sh[warp][lane] = acc;
   __syncwarp();
@@ -691,9 +709,10 @@ int launch_bwd(int N, const BwdArgs& a, long long T, cudaStream_t s) {
 }
 
 int launch_segsum(const float* part, int RP, const long long* goff, int Ge, const int32_t* perm,
-                  float* gsum, cudaStream_t s) {
+                  long long n_cap, int* status, float* gsum, cudaStream_t s) {
   if (Ge <= 0) return 0;
-  segsum_kernel<<<(unsigned)ceil_div<long long>(Ge, 8), 256, 0, s>>>(part, RP, goff, Ge, perm, gsum);
+  segsum_kernel<<<(unsigned)ceil_div<long long>(Ge, 8), 256, 0, s>>>(part, RP, goff, Ge, perm,
+                                                                    n_cap, status, gsum);
   return 1;
 }
 

@@ -150,7 +150,7 @@ int launch_loss(const float* y, const float* target, float* dy, long long n, dou
 int launch_bwd(int N, const BwdArgs& a, long long T, cudaStream_t s);
 int launch_selftest_wait(int* status, int which, cudaStream_t s);
 int launch_segsum(const float* part, int RP, const long long* goff, int Ge, const int32_t* perm,
-                 float* gsum, cudaStream_t s);
+                  long long n_cap, int* status, float* gsum, cudaStream_t s);
 int launch_chain(int N, const ChainArgs& a, cudaStream_t s);
 int launch_adam(const AdamArgs& a, cudaStream_t s);
 int launch_densify(int N, const DensifyArgs& a, cudaStream_t s);

@@ -108,7 +108,7 @@ EXPORTS = ["ndg_workspace_size", "ndg_build_cull", "ndg_build_cull_conditioned",
            "ndg_loss_l2", "ndg_loss_rel_l2", "ndg_backward", "ndg_adam", "ndg_densify",
            "ndg_read_status", "ndg_status_string", "ndg_version", "ndg_forward_noalloc",
            "ndg_selftest_timeout", "ndg_probe_pipe", "ndg_loss_l2_shard",
-           "ndg_batch_workspace_size", "ndg_forward_batch"]
+           "ndg_batch_workspace_size", "ndg_forward_batch", "ndg_backward_order"]
 NDG_ERR_SCRATCH_LIMIT = 7
 
 
@@ -139,6 +139,7 @@ def lib():
                                ctypes.c_float, _P, TR]
         L.ndg_densify.argtypes = [M, ctypes.c_float, ctypes.c_float, _P, M, M, _P, _P, sz, _P, TR]
         L.ndg_forward_noalloc.argtypes = [M, Qp, C, _P, _P]
+        L.ndg_backward_order.argtypes = [M, Qp, C, _P, sz, _P, TR]
         L.ndg_batch_workspace_size.argtypes = [ctypes.c_int]
         L.ndg_batch_workspace_size.restype = sz
         L.ndg_forward_batch.argtypes = [ctypes.POINTER(FrameC), ctypes.c_int, _P, sz, _P, _P, TR]
@@ -152,7 +153,8 @@ def lib():
         for name in ["ndg_build_cull", "ndg_build_cull_conditioned", "ndg_forward", "ndg_loss_l2",
                      "ndg_loss_rel_l2", "ndg_backward", "ndg_adam", "ndg_densify",
                      "ndg_read_status", "ndg_forward_noalloc", "ndg_selftest_timeout",
-                     "ndg_probe_pipe", "ndg_loss_l2_shard", "ndg_forward_batch"]:
+                     "ndg_probe_pipe", "ndg_loss_l2_shard", "ndg_forward_batch",
+                     "ndg_backward_order"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -427,6 +429,19 @@ def backward(mix: Mixture, x: torch.Tensor, tile: int, cull: Cull, dy: torch.Ten
     _check(lib().ndg_backward(ctypes.byref(mix.c()), ctypes.byref(queries_c(x, tile)),
                               ctypes.byref(cull.c()), mode, _ptr(dy), ctypes.byref(grad.c()),
                               _ptr(ws), ws.numel(), _stream(stream), _tr(trace)), "ndg_backward")
+
+
+NDG_BWD_ORDER_READY = 0x100
+
+
+def backward_order(mix: Mixture, x: torch.Tensor, tile: int, cull: Cull, ws: torch.Tensor,
+                   stream=None, trace: Trace | None = None):
+    """ndg_backward_order: the Gaussian-major order of the entries, computed
+    ahead of backward(..., mode | NDG_BWD_ORDER_READY) (e.g. on a side
+    stream while the forward runs)."""
+    _check(lib().ndg_backward_order(ctypes.byref(mix.c()), ctypes.byref(queries_c(x, tile)),
+                                    ctypes.byref(cull.c()), _ptr(ws), ws.numel(), _stream(stream),
+                                    _tr(trace)), "ndg_backward_order")
 
 
 def adam(params: Mixture, grad: Mixture, m1: Mixture, m2: Mixture, step: torch.Tensor, lr: float,

@@ -511,6 +511,39 @@ def test_backward_above_32768_tiles_matches_oracle(ndg, oracle, mode):
     grad2 = ev.backward(gm, dyt, mode=md)
     for n in NAMES:
         assert torch.equal(getattr(grad, n), getattr(grad2, n)), n
+    # the radix-sorted order computed ahead (ndg_backward_order), then used
+    ndg.backward_order(gm, xt, tile, ev.cull, ev.ws)
+    grad3 = ev.backward(gm, dyt, mode=md | ndg.NDG_BWD_ORDER_READY)
+    assert ndg.read_status(ev.ws) == 0
+    for n in NAMES:
+        assert torch.equal(getattr(grad, n), getattr(grad3, n)), n
+
+
+@pytest.mark.parametrize("N,mode", [(6, "tc"), (6, "fp32"), (10, "tc")])
+def test_backward_order_ahead_on_a_side_stream(ndg, N, mode):
+    """ndg_backward_order on a second stream while the forward runs, then
+    ndg_backward with NDG_BWD_ORDER_READY: gradients bit-identical to the
+    backward that orders the entries itself."""
+    import torch
+    G, Q, tile, k = 800, 8192, 256, 16
+    seed = 930 + N
+    mix, ch, x = make_case(N, G, Q, seed, children=True)
+    gm, xt, proj, cp, ev, E = gpu_setup(ndg, N, mix, ch, x, tile, k, 1 / 255, 3.0, 64, seed)
+    md = ndg.NDG_MODE_TC if mode == "tc" else ndg.NDG_MODE_FP32
+    dyt = torch.as_tensor((synth.rng(seed + 1).standard_normal((Q, 3)) / (3 * Q))
+                          .astype(np.float32)).cuda()
+    want = ev.backward(gm, dyt, mode=md)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    ndg.backward_order(gm, xt, tile, ev.cull, ev.ws, stream=side)
+    ev.forward(gm, mode=md)  # on the current stream, beside the order
+    torch.cuda.current_stream().wait_stream(side)
+    got = ev.backward(gm, dyt, mode=md | ndg.NDG_BWD_ORDER_READY)
+    torch.cuda.synchronize()
+    assert ndg.read_status(ev.ws) == 0
+    for n in NAMES:
+        assert torch.equal(getattr(want, n), getattr(got, n)), n
 
 
 def test_non_finite_parameter_sets_numeric_status(ndg):
