@@ -95,6 +95,34 @@ def test_invalid_arguments_rejected_on_host(ndg):
     assert L.ndg_selftest_timeout(2, ws, BIG, None) == 1  # unknown wait kind
 
 
+def test_backward_order_host_checks(ndg):
+    """ndg_backward_order applies ndg_backward's argument and workspace rules
+    before any CUDA call; the order flag is the header's."""
+    L = ndg.lib()
+    src = open(os.path.join(ROOT, "include", "ndg.h")).read()
+    flag = int(re.search(r"#define\s+NDG_BWD_ORDER_READY\s+(0x[0-9a-fA-F]+|\d+)", src).group(1), 0)
+    assert flag == ndg.NDG_BWD_ORDER_READY
+    assert flag & (ndg.NDG_MODE_FP32 | ndg.NDG_MODE_TC | ndg.NDG_MODE_AUTO) == 0
+    m = _mix_c(ndg)
+    q = ndg.QueriesC(100, 256, ctypes.c_void_p(0x2000))
+    cull = ndg.CullC(ctypes.c_void_p(0x4000), ctypes.c_void_p(0x5000), 100, ctypes.c_void_p(0x6000))
+    ws = ctypes.c_void_p(0x100000)
+    BIG = 1 << 40
+    E = ndg.NDG_ERR_INVALID_ARG
+    assert L.ndg_backward_order(ctypes.byref(_mix_c(ndg, N=13)), ctypes.byref(q),
+                                ctypes.byref(cull), ws, BIG, None, None) == E
+    assert L.ndg_backward_order(ctypes.byref(m), ctypes.byref(q), ctypes.byref(cull), None, BIG,
+                                None, None) == E
+    assert L.ndg_backward_order(ctypes.byref(m), ctypes.byref(q), ctypes.byref(cull),
+                                ctypes.c_void_p(0x100010), BIG, None, None) == E
+    huge = ndg.CullC(ctypes.c_void_p(0x4000), ctypes.c_void_p(0x5000), 1 << 31,
+                     ctypes.c_void_p(0x6000))
+    assert L.ndg_backward_order(ctypes.byref(m), ctypes.byref(q), ctypes.byref(huge), ws, BIG,
+                                None, None) == E  # E_cap must stay below 2^31
+    assert L.ndg_backward_order(ctypes.byref(m), ctypes.byref(q), ctypes.byref(cull), ws, 1024,
+                                None, None) == ndg.NDG_ERR_WORKSPACE
+
+
 def test_mode_constants_match_header(ndg):
     """The binding's mode numbers and AUTO threshold are the header's."""
     import os
