@@ -590,6 +590,23 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
 #pragma unroll
     for (int d = 0; d < N; ++d) hsc[d] = sh[d];
     float back = 1.0f;
+    // one unit's UQ / 2 columns of this warp: E = 2^(s back) to FP16 in place
+    auto block = [&](uint32_t col, uint32_t* v, auto sc_tag) {
+      constexpr bool SC = decltype(sc_tag)::value;
+      constexpr int WC = S::UQ / 2;
+#pragma unroll
+      for (int cb = 0; cb < WC; cb += 32) {
+        uint32_t hi[16];
+#pragma unroll
+        for (int p = 0; p < 16; ++p) {
+          float2 sv = make_float2(__uint_as_float(v[cb + 2 * p]), __uint_as_float(v[cb + 2 * p + 1]));
+          if constexpr (SC) sv = __fmul2_rn(sv, make_float2(back, back));
+          const __half2 e2 = __floats2half2_rn(ex2_approx(sv.x), ex2_approx(sv.y));
+          hi[p] = *reinterpret_cast<const uint32_t*>(&e2);
+        }
+        tmem_st16(col + (uint32_t)cb, hi);
+      }
+    };
     bool ok = true;
     for (int u = 0; u < U; ++u) {
       const int i = u / nh, h = u - i * nh, s = i % CS, sb = u % S::NBUF;
@@ -610,19 +627,10 @@ __global__ void __launch_bounds__(416, 1) bwd_h_kernel(BwdArgs a) {
       tmem_wait_ld();
 #pragma unroll
       for (int cb = 0; cb < WC; cb += 16) tmem_reg_fence16(v + cb);
-#pragma unroll
-      for (int cb = 0; cb < WC; cb += 32) {
-        uint32_t hi[16];
-#pragma unroll
-        for (int p = 0; p < 16; ++p) {
-          const float2 sv = __fmul2_rn(make_float2(__uint_as_float(v[cb + 2 * p]),
-                                                   __uint_as_float(v[cb + 2 * p + 1])),
-                                       make_float2(back, back));
-          const __half2 e2 = __floats2half2_rn(ex2_approx(sv.x), ex2_approx(sv.y));
-          hi[p] = *reinterpret_cast<const uint32_t*>(&e2);
-        }
-        tmem_st16(col + (uint32_t)cb, hi);
-      }
+      // rows scaled down to fit FP16 (rare) multiply s back; a warp without
+      // such a row skips the multiply
+      if (__all_sync(0xffffffffu, back == 1.0f)) block(col, v, BoolTag<false>{});
+      else block(col, v, BoolTag<true>{});
       tmem_wait_st();
       fence_before_sync();
       warp_arrive(&e_full[sb]);

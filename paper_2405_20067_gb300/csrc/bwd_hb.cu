@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(416, 1) bwd_hb_kernel(BwdArgs a) {
     // (hi + lo blocks summed), dl/dw_c = dys (sum of the two halves' e dy').
     // the chain's per-candidate stash row and sum_q e dy' (captured, so that
     // they stay in registers)
-    float sv[N + 6], gw[3];
+    float sv[N + 6] = {}, gw[3] = {};
     auto part = [&](int ic, auto gtag) {
       constexpr int GG = decltype(gtag)::value;
       constexpr int p0 = GG * S::PARTW;
@@ -660,6 +660,36 @@ __global__ void __launch_bounds__(416, 1) bwd_hb_kernel(BwdArgs a) {
     };
     float back = 1.0f, w0 = 0.f, w1 = 0.f, w2 = 0.f;
     float2 g0 = make_float2(0.f, 0.f), g1 = g0, g2 = g0;
+    // one unit's 64 columns of this warp: e = 2^(s back), beta' to FP16 in
+    // place (the first 16 columns of each 32-query block), sum_q e dy'
+    auto block = [&](uint32_t col, int q0, uint32_t* v, auto sc_tag) {
+      constexpr bool SC = decltype(sc_tag)::value;
+      constexpr int WC = S::UQ / 2;
+#pragma unroll
+      for (int cb = 0; cb < WC; cb += 32) {
+        uint32_t bw[16];
+#pragma unroll
+        for (int p = 0; p < 16; ++p) {
+          const int q = q0 + cb + 2 * p;
+          float2 sv2 = make_float2(__uint_as_float(v[cb + 2 * p]), __uint_as_float(v[cb + 2 * p + 1]));
+          if constexpr (SC) sv2 = __fmul2_rn(sv2, make_float2(back, back));
+          const float2 e = make_float2(ex2_approx(sv2.x), ex2_approx(sv2.y));
+          const float2 d0 = *reinterpret_cast<const float2*>(sdyc + q);
+          const float2 d1 = *reinterpret_cast<const float2*>(sdyc + 256 + q);
+          const float2 d2 = *reinterpret_cast<const float2*>(sdyc + 512 + q);
+          float2 tw = __fmul2_rn(d0, make_float2(w0, w0));
+          tw = __ffma2_rn(d1, make_float2(w1, w1), tw);
+          tw = __ffma2_rn(d2, make_float2(w2, w2), tw);
+          const float2 be = __fmul2_rn(e, tw);
+          g0 = __ffma2_rn(e, d0, g0);
+          g1 = __ffma2_rn(e, d1, g1);
+          g2 = __ffma2_rn(e, d2, g2);
+          const __half2 bh = __floats2half2_rn(be.x, be.y);
+          bw[p] = *reinterpret_cast<const uint32_t*>(&bh);
+        }
+        tmem_st16(col + (uint32_t)cb, bw);
+      }
+    };
     bool ok = true;
     for (int u = 0; u < U; ++u) {
       const int i = u / nh, h = u - i * nh, sb = u % NBUF;
@@ -684,32 +714,12 @@ __global__ void __launch_bounds__(416, 1) bwd_hb_kernel(BwdArgs a) {
       tmem_wait_ld();
 #pragma unroll
       for (int cb = 0; cb < WC; cb += 16) tmem_reg_fence16(v + cb);
-#pragma unroll
-      for (int cb = 0; cb < WC; cb += 32) {
-        uint32_t bw[16];
-#pragma unroll
-        for (int p = 0; p < 16; ++p) {
-          const int q = q0 + cb + 2 * p;
-          const float2 sv2 = __fmul2_rn(make_float2(__uint_as_float(v[cb + 2 * p]),
-                                                    __uint_as_float(v[cb + 2 * p + 1])),
-                                        make_float2(back, back));
-          const float2 e = make_float2(ex2_approx(sv2.x), ex2_approx(sv2.y));
-          const float2 d0 = *reinterpret_cast<const float2*>(sdyc + q);
-          const float2 d1 = *reinterpret_cast<const float2*>(sdyc + 256 + q);
-          const float2 d2 = *reinterpret_cast<const float2*>(sdyc + 512 + q);
-          float2 tw = __fmul2_rn(d0, make_float2(w0, w0));
-          tw = __ffma2_rn(d1, make_float2(w1, w1), tw);
-          tw = __ffma2_rn(d2, make_float2(w2, w2), tw);
-          const float2 be = __fmul2_rn(e, tw);
-          g0 = __ffma2_rn(e, d0, g0);
-          g1 = __ffma2_rn(e, d1, g1);
-          g2 = __ffma2_rn(e, d2, g2);
-          const __half2 bh = __floats2half2_rn(be.x, be.y);
-          bw[p] = *reinterpret_cast<const uint32_t*>(&bh);
-        }
-        tmem_st16(col + (uint32_t)cb, bw);
-      }
+      // rows scaled down to fit FP16 (rare) multiply s back; a warp without
+      // such a row skips the multiply
+      if (__all_sync(0xffffffffu, back == 1.0f)) block(col, q0, v, BoolTag<false>{});
+      else block(col, q0, v, BoolTag<true>{});
       tmem_wait_st();
+
       if (h == nh - 1) {
         // this warp's half of sum_q e dy' for the chunk's candidates
         float4* gd = reinterpret_cast<float4*>(slot_f(i) + NC * SV) + grp * NC + j;
