@@ -49,12 +49,12 @@ def workload_name(g, q):
 
 
 # DRAM bytes per candidate entry of one bwd_h_kernel<6> launch:
-# dram__bytes_read.sum + dram__bytes_write.sum = 36.69 MB + 621.15 MB from one
-# ncu capture of the 1/8 workload (5,211,201 entries), i.e. 126.2 B per entry;
-# a full launch's traffic is this times its entries (the kernel streams one
-# gradient record per entry, so traffic grows in proportion).  To be re-taken
-# whenever the kernel changes.
-BWD_BYTES_PER_ENTRY = (36.690944e6 + 621.153792e6) / 5211201
+# dram__bytes_read.sum + dram__bytes_write.sum = 36.69 MB + 621.08 MB from one
+# ncu capture of the 1/8 workload (5,196,498 entries in that run's step),
+# i.e. 126.6 B per entry; a full launch's traffic is this times its entries
+# (the kernel streams one gradient record per entry, so traffic grows in
+# proportion).  To be re-taken whenever the kernel changes.
+BWD_BYTES_PER_ENTRY = (36.689408e6 + 621.075456e6) / 5196498
 
 
 def flops_per_pair(N: int):
