@@ -521,8 +521,9 @@ ndg_status ndg_forward_batch(const ndg_frame* frames, int n_frames, void* batch_
   b.n_frames = n_frames;
   b.n_items = items;
   int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    return NDG_ERR_CUDA;
   const int grid = (int)(items < (long long)sms ? items : (long long)sms);
   tr.begin();
   tr += launch_fwd_tc_batch(b, smem, grid, s);
