@@ -467,6 +467,11 @@ ndg_status ndg_forward_batch(const ndg_frame* frames, int n_frames, void* batch_
     if (fr.ws_bytes < common_layout(make_sizes(fr.mix, fr.q, nullptr, 0)).end)
       return NDG_ERR_WORKSPACE;
   }
+  // one persistent CTA per SM (queried before anything is launched)
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    return NDG_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
   Tracer tr(trace, s);
   std::vector<char> img(bl.end, 0);
@@ -520,10 +525,6 @@ ndg_status ndg_forward_batch(const ndg_frame* frames, int n_frames, void* batch_
   b.stamps = stamps;
   b.n_frames = n_frames;
   b.n_items = items;
-  int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
-    return NDG_ERR_CUDA;
   const int grid = (int)(items < (long long)sms ? items : (long long)sms);
   tr.begin();
   tr += launch_fwd_tc_batch(b, smem, grid, s);
