@@ -546,6 +546,38 @@ def test_backward_order_ahead_on_a_side_stream(ndg, N, mode):
         assert torch.equal(getattr(want, n), getattr(got, n)), n
 
 
+def test_backward_with_a_stale_order_stays_inside_its_buffers(ndg):
+    """NDG_BWD_ORDER_READY with an order left from other lists (a caller
+    error): the segmented sum clamps segment bounds and checks entry indices
+    against the capacity, so the call completes, reads nothing outside the
+    workspace and may report NDG_ERR_INVALID_ARG; the next backward that
+    orders the entries itself is correct again."""
+    import torch
+    N, G, Q, tile, k = 6, 800, 8192, 256, 16
+    seed = 940
+    mix, ch, x = make_case(N, G, Q, seed, children=True)
+    gm, xt, proj, cp, ev, E = gpu_setup(ndg, N, mix, ch, x, tile, k, 1 / 255, 3.0, 64, seed)
+    dyt = torch.as_tensor((synth.rng(seed + 1).standard_normal((Q, 3)) / (3 * Q))
+                          .astype(np.float32)).cuda()
+    want = ev.backward(gm, dyt, mode=ndg.NDG_MODE_TC)
+    ndg.backward_order(gm, xt, tile, ev.cull, ev.ws)
+    # other lists in the same buffers: queries shifted, so the tiles' candidates change
+    x0 = xt.clone()
+    xt.add_(0.25)
+    E2 = ev.build(gm)
+    assert E2 <= ev.E_cap
+    ev.backward(gm, dyt, mode=ndg.NDG_MODE_TC | ndg.NDG_BWD_ORDER_READY)
+    torch.cuda.synchronize()
+    assert ndg.read_status(ev.ws) in (ndg.NDG_OK, ndg.NDG_ERR_INVALID_ARG)
+    xt.copy_(x0)
+    assert ev.build(gm) == E
+    again = ev.backward(gm, dyt, mode=ndg.NDG_MODE_TC)
+    torch.cuda.synchronize()
+    assert ndg.read_status(ev.ws) == ndg.NDG_OK
+    for n in NAMES:
+        assert torch.equal(getattr(want, n), getattr(again, n)), n
+
+
 def test_non_finite_parameter_sets_numeric_status(ndg):
     """A raw parameter whose activation is not finite (NaN, or +inf
     brightness; planted on the host) makes the preparation report
