@@ -190,9 +190,19 @@ ndg_status ndg_build_cull_conditioned(const ndg_mixture* mix, const ndg_queries*
  * for N = 10. */
 #define NDG_AUTO_MIN_CANDIDATES(N) ((N) <= 6 ? 192 : 128)
 
+/* Mode flag for ndg_forward and ndg_backward: the prepared per-Gaussian
+ * records in `ws` are those that ndg_build_cull (or
+ * ndg_build_cull_conditioned) wrote there from these same parameters, with
+ * no call on this workspace in between that prepares records of another
+ * mixture; the call then skips its own preparation (the records are the same
+ * values either way).  ndg_backward uses it in NDG_MODE_TC and ignores it in
+ * NDG_MODE_FP32. */
+#define NDG_RECORDS_READY 0x200
+
 /* Eq. 1 and Eq. 8: y [Q][3] = culled mixture sum at every query.  `cull`
  * must come from ndg_build_cull on the same mixture and queries.  mode:
- * NDG_MODE_FP32, NDG_MODE_TC or NDG_MODE_AUTO (else NDG_ERR_INVALID_ARG). */
+ * NDG_MODE_FP32, NDG_MODE_TC or NDG_MODE_AUTO (else NDG_ERR_INVALID_ARG),
+ * optionally with NDG_RECORDS_READY. */
 ndg_status ndg_forward(const ndg_mixture* mix, const ndg_queries* q,
                        const ndg_cull* cull, int mode, float* y, void* ws,
                        size_t ws_bytes, ndg_stream stream, ndg_trace* trace);
@@ -259,7 +269,7 @@ ndg_status ndg_backward_order(const ndg_mixture* mix, const ndg_queries* q, cons
  * lifted coefficients and of w come from a second contraction E Psi with
  * Psi = dy (x) phi; above, from beta Phi with beta = e sum_c dy_c w_c and
  * dl/dw summed in FP32); NDG_MODE_AUTO: NDG_MODE_TC; any of them may carry
- * NDG_BWD_ORDER_READY.  Tensor-core gradients are within ~6e-4 relative of
+ * NDG_BWD_ORDER_READY and NDG_RECORDS_READY.  Tensor-core gradients are within ~6e-4 relative of
  * the FP64 definition per tensor. */
 ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q,
                         const ndg_cull* cull, int mode, const float* dy,

@@ -309,6 +309,11 @@ ndg_status build_cull(const ndg_mixture* mix, const ndg_queries* q, const ndg_cu
   pa.bin = (uint32_t*)(w + L.bin);
   pa.status = status;
   pa.xc = xc;
+  // the records of every evaluation form (A, m, w, then M) as well, so that
+  // an evaluation or backward of the same parameters may skip its own
+  // preparation (NDG_RECORDS_READY)
+  pa.rec = (float*)(w + c.rec);
+  pa.rec_kind = 2;
   tr += launch_prep(N, pa, s);
   uint32_t* sk;
   int32_t* sv;
@@ -367,6 +372,8 @@ ndg_status ndg_forward(const ndg_mixture* mix, const ndg_queries* q, const ndg_c
                        float* y, void* ws, size_t ws_bytes, ndg_stream stream,
                        ndg_trace* trace) {
   ndg_status st;
+  const bool recs_ready = (mode & NDG_RECORDS_READY) != 0;
+  mode &= ~NDG_RECORDS_READY;
   if ((st = check_mix(mix)) || (st = check_queries(q)) || (st = check_cull(cull))) return st;
   if (mode != NDG_MODE_FP32 && mode != NDG_MODE_TC && mode != NDG_MODE_AUTO)
     return NDG_ERR_INVALID_ARG;
@@ -380,10 +387,12 @@ ndg_status ndg_forward(const ndg_mixture* mix, const ndg_queries* q, const ndg_c
   char* w = (char*)ws;
   PrepArgs pa = prep_args(mix);
   pa.rec = (float*)(w + c.rec);
-  // AUTO: records with both A (tensor-core form) and M (FP32 form)
-  pa.rec_kind = mode == NDG_MODE_AUTO ? 2 : (mode == NDG_MODE_TC ? 1 : 0);
+  // AUTO, or records left by ndg_build_cull: both A (tensor-core form) and
+  // M (FP32 form) per record
+  const bool kind2 = recs_ready || mode == NDG_MODE_AUTO;
+  pa.rec_kind = kind2 ? 2 : (mode == NDG_MODE_TC ? 1 : 0);
   pa.status = &reinterpret_cast<WsHeader*>(w + c.header)->status;
-  tr += launch_prep(mix->N, pa, s);
+  if (!recs_ready) tr += launch_prep(mix->N, pa, s);
   FwdArgs fa{};
   fa.x = q->x;
   fa.Q = q->Q;
@@ -415,6 +424,10 @@ ndg_status ndg_forward(const ndg_mixture* mix, const ndg_queries* q, const ndg_c
     tr += launch_fwd(mix->N, ff, z.T, s);
     tr.end();
     return cuda_ok();
+  }
+  if (kind2) {
+    fa.rec_stride4 = rec_tc_floats(mix->N) / 4;
+    if (mode == NDG_MODE_FP32) fa.mat_off4 = rec_floats(mix->N) / 4;
   }
   tr.begin();
   tr += mode == NDG_MODE_TC ? launch_fwd_tc(mix->N, fa, z.T, s) : launch_fwd(mix->N, fa, z.T, s);
@@ -650,7 +663,8 @@ ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q, const ndg_
                         ndg_stream stream, ndg_trace* trace) {
   ndg_status st;
   const bool order_ready = (mode & NDG_BWD_ORDER_READY) != 0;
-  mode &= ~NDG_BWD_ORDER_READY;
+  const bool recs_ready = (mode & NDG_RECORDS_READY) != 0;
+  mode &= ~(NDG_BWD_ORDER_READY | NDG_RECORDS_READY);
   if ((st = check_backward_args(mix, q, cull, ws, ws_bytes))) return st;
   if (mode == NDG_MODE_AUTO) mode = NDG_MODE_TC;
   if (mode != NDG_MODE_FP32 && mode != NDG_MODE_TC) return NDG_ERR_INVALID_ARG;
@@ -669,7 +683,8 @@ ndg_status ndg_backward(const ndg_mixture* mix, const ndg_queries* q, const ndg_
   pa.rec = (float*)(w + c.rec);
   pa.rec_kind = mode == NDG_MODE_TC ? 2 : 0;
   pa.status = &reinterpret_cast<WsHeader*>(w + c.header)->status;
-  tr += launch_prep(N, pa, s);
+  // the tensor-core form reads the records ndg_build_cull leaves (same kind)
+  if (!(recs_ready && mode == NDG_MODE_TC)) tr += launch_prep(N, pa, s);
   const int Ge = pa.Ge;
   int32_t* sv;
   long long* goff = (long long*)(w + L.goff);

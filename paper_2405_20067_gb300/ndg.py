@@ -432,6 +432,7 @@ def backward(mix: Mixture, x: torch.Tensor, tile: int, cull: Cull, dy: torch.Ten
 
 
 NDG_BWD_ORDER_READY = 0x100
+NDG_RECORDS_READY = 0x200  # the records ndg_build_cull left in ws are current
 
 
 def backward_order(mix: Mixture, x: torch.Tensor, tile: int, cull: Cull, ws: torch.Tensor,

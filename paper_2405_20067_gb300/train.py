@@ -142,7 +142,10 @@ class Trainer:
         if target is not None:
             self.target.copy_(target, non_blocking=True)
         mix = self.mix
-        self.ev.mode, self.ev.bwd_mode = self.mode, self.bwd_mode
+        # the cull prepares the records the evaluation and the backward read
+        # (the parameters do not change in between)
+        self.ev.mode = self.mode | ndg.NDG_RECORDS_READY
+        self.ev.bwd_mode = self.bwd_mode | ndg.NDG_RECORDS_READY
         ndg.build_cull(mix, self.x, self.tile, self.cp, self.ev.cull, self.ev.ws,
                        trace=self._tr("build_cull"))
         if self.overlap_order:

@@ -546,6 +546,35 @@ def test_backward_order_ahead_on_a_side_stream(ndg, N, mode):
         assert torch.equal(getattr(want, n), getattr(got, n)), n
 
 
+@pytest.mark.parametrize("N", [6, 10])
+def test_records_prepared_by_the_cull_are_reused_exactly(ndg, N):
+    """NDG_RECORDS_READY: after ndg_build_cull the evaluation (every form)
+    and the tensor-core backward skip their own preparation and give the
+    same outputs and gradients, bit for bit."""
+    import torch
+    G, Q, tile, k = 900, 8192, 256, 16
+    seed = 950 + N
+    mix, ch, x = make_case(N, G, Q, seed, children=True)
+    gm, xt, proj, cp, ev, E = gpu_setup(ndg, N, mix, ch, x, tile, k, 1 / 255, 3.0, 64, seed)
+    dyt = torch.as_tensor((synth.rng(seed + 1).standard_normal((Q, 3)) / (3 * Q))
+                          .astype(np.float32)).cuda()
+    for md in (ndg.NDG_MODE_TC, ndg.NDG_MODE_FP32, ndg.NDG_MODE_AUTO):
+        want = ev.forward(gm, mode=md).clone()
+        ev.build(gm)  # leaves the records
+        got = ev.forward(gm, mode=md | ndg.NDG_RECORDS_READY)
+        assert torch.equal(want, got), md
+    want = ev.backward(gm, dyt, mode=ndg.NDG_MODE_TC)
+    ev.build(gm)
+    tr = ndg.Trace()
+    got = ndg.Mixture.zeros_like(gm)
+    ndg.backward(gm, xt, tile, ev.cull, dyt, got, ev.ws,
+                 mode=ndg.NDG_MODE_TC | ndg.NDG_RECORDS_READY, trace=tr)
+    torch.cuda.synchronize()
+    assert ndg.read_status(ev.ws) == ndg.NDG_OK
+    for n in NAMES:
+        assert torch.equal(getattr(want, n), getattr(got, n)), n
+
+
 def test_backward_with_a_stale_order_stays_inside_its_buffers(ndg):
     """NDG_BWD_ORDER_READY with an order left from other lists (a caller
     error): the segmented sum clamps segment bounds and checks entry indices
