@@ -103,6 +103,9 @@ def test_backward_order_host_checks(ndg):
     flag = int(re.search(r"#define\s+NDG_BWD_ORDER_READY\s+(0x[0-9a-fA-F]+|\d+)", src).group(1), 0)
     assert flag == ndg.NDG_BWD_ORDER_READY
     assert flag & (ndg.NDG_MODE_FP32 | ndg.NDG_MODE_TC | ndg.NDG_MODE_AUTO) == 0
+    rflag = int(re.search(r"#define\s+NDG_RECORDS_READY\s+(0x[0-9a-fA-F]+|\d+)", src).group(1), 0)
+    assert rflag == ndg.NDG_RECORDS_READY
+    assert rflag & (flag | ndg.NDG_MODE_FP32 | ndg.NDG_MODE_TC | ndg.NDG_MODE_AUTO) == 0
     m = _mix_c(ndg)
     q = ndg.QueriesC(100, 256, ctypes.c_void_p(0x2000))
     cull = ndg.CullC(ctypes.c_void_p(0x4000), ctypes.c_void_p(0x5000), 100, ctypes.c_void_p(0x6000))
