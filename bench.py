@@ -354,13 +354,18 @@ def run_fit(form: str, steps: int, warmup: int, device: str, flush, world: int, 
     torch.cuda.synchronize()
     tr.check()
     # per-kernel times and launch counts: traced eager steps (CUDA events
-    # around each call's main kernel on the launching stream)
+    # around each call's main kernel on the launching stream), with the
+    # backward's order computed inside the backward (not beside the forward),
+    # so that each kernel's time is its own and every launch is counted
     ntr = max(3, steps // 4)
     traces = [{n: ndg.Trace() for n in names} for _ in range(ntr)]
+    overlap = tr.overlap_order
+    tr.overlap_order = False
     for i in range(ntr):
         flush.zero_()
         one_step(traces[i])
     torch.cuda.synchronize()
+    tr.overlap_order = overlap
     kern = {n: statistics.mean(tr_[n].ms() for tr_ in traces) for n in names}
     launches_per_step = sum(tr_[n].launches for tr_ in traces for n in names) / ntr
     # the timed steps: the whole step captured once as a CUDA graph and replayed
