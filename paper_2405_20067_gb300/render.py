@@ -77,7 +77,9 @@ class Frame:
         form, tile = cfg
         ev = self.evaluator(tile)
         ndg.build_cull(self.mix, self.x, tile, self.cp, ev.cull, ev.ws)
-        ndg.forward(self.mix, self.x, tile, ev.cull, self.y, ev.ws, mode=_MODES[form])
+        # the cull has just prepared the records from the same parameters
+        ndg.forward(self.mix, self.x, tile, ev.cull, self.y, ev.ws,
+                    mode=_MODES[form] | ndg.NDG_RECORDS_READY)
         return self.y
 
     def time(self, cfg: tuple, reps: int = 1) -> float:
