@@ -190,12 +190,13 @@ ndg_status ndg_build_cull_conditioned(const ndg_mixture* mix, const ndg_queries*
  * for N = 10. */
 #define NDG_AUTO_MIN_CANDIDATES(N) ((N) <= 6 ? 192 : 128)
 
-/* Mode flag for ndg_forward and ndg_backward: the prepared per-Gaussian
- * records in `ws` are those that ndg_build_cull (or
- * ndg_build_cull_conditioned) wrote there from these same parameters, with
- * no call on this workspace in between that prepares records of another
- * mixture; the call then skips its own preparation (the records are the same
- * values either way).  ndg_backward uses it in NDG_MODE_TC and ignores it in
+/* Mode flag for ndg_forward and ndg_backward (and ndg_frame.flags): the
+ * prepared per-Gaussian records in `ws` are those that ndg_build_cull (or
+ * ndg_build_cull_conditioned) wrote there from these same parameters, and
+ * no call on this workspace since has prepared records itself (an
+ * ndg_forward or ndg_backward without this flag rewrites them in its own
+ * layout); the call then skips its own preparation (the values are the same
+ * either way).  ndg_backward uses it in NDG_MODE_TC and ignores it in
  * NDG_MODE_FP32. */
 #define NDG_RECORDS_READY 0x200
 
@@ -339,6 +340,8 @@ typedef struct ndg_frame {
   void* ws;             /* this frame's workspace: at least
                            ndg_workspace_size(mix, q, NULL, 0) bytes */
   size_t ws_bytes;
+  int flags;            /* 0, or NDG_RECORDS_READY: the records this
+                           frame's cull left in ws are current */
 } ndg_frame;
 
 /* Bytes of the batch descriptor workspace of ndg_forward_batch. */

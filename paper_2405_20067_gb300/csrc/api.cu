@@ -479,6 +479,7 @@ ndg_status ndg_forward_batch(const ndg_frame* frames, int n_frames, void* batch_
     if (!fr.ws || !aligned(fr.ws, kAlign)) return NDG_ERR_INVALID_ARG;
     if (fr.ws_bytes < common_layout(make_sizes(fr.mix, fr.q, nullptr, 0)).end)
       return NDG_ERR_WORKSPACE;
+    if (fr.flags & ~NDG_RECORDS_READY) return NDG_ERR_INVALID_ARG;
   }
   // one persistent CTA per SM (queried before anything is launched)
   int dev = 0, sms = 0;
@@ -500,10 +501,14 @@ ndg_status ndg_forward_batch(const ndg_frame* frames, int n_frames, void* batch_
     char* w = (char*)fr.ws;
     PrepArgs pa = prep_args(fr.mix);
     pa.rec = (float*)(w + c.rec);
-    pa.rec_kind = 1;  // the tensor-core form's records
+    // the tensor-core form's records, or those of every form that the
+    // frame's cull left there
+    const bool ready = (fr.flags & NDG_RECORDS_READY) != 0;
+    pa.rec_kind = ready ? 2 : 1;
     pa.status = &reinterpret_cast<WsHeader*>(w + c.header)->status;
-    tr += launch_prep(fr.mix->N, pa, s);
+    if (!ready) tr += launch_prep(fr.mix->N, pa, s);
     FwdArgs& a = fa[f];
+    a.rec_stride4 = ready ? rec_tc_floats(fr.mix->N) / 4 : 0;
     a.x = fr.q->x;
     a.Q = fr.q->Q;
     a.tile = fr.q->tile_size;

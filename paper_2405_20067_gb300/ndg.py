@@ -70,7 +70,8 @@ class CullC(ctypes.Structure):
 
 class FrameC(ctypes.Structure):
     _fields_ = [("mix", ctypes.POINTER(MixtureC)), ("q", ctypes.POINTER(QueriesC)),
-                ("cull", ctypes.POINTER(CullC)), ("y", _P), ("ws", _P), ("ws_bytes", ctypes.c_size_t)]
+                ("cull", ctypes.POINTER(CullC)), ("y", _P), ("ws", _P), ("ws_bytes", ctypes.c_size_t),
+                ("flags", ctypes.c_int)]
 
 
 class TraceC(ctypes.Structure):
@@ -347,18 +348,21 @@ def batch_workspace(n_frames: int, device="cuda") -> torch.Tensor:
 
 
 def forward_batch(frames, batch_ws: torch.Tensor, stamps: torch.Tensor | None = None,
-                  stream=None, trace: Trace | None = None):
+                  stream=None, trace: Trace | None = None, records_ready: bool = False):
     """ndg_forward_batch: the tensor-core forward of many frames in one
     persistent launch.  frames: sequence of (mix, x, tile, cull, y, ws), each
     as for forward(); stamps: int64 [1 + len(frames)] on the device or None
-    (%globaltimer ns: [0] launch start, [1 + f] frame f complete)."""
+    (%globaltimer ns: [0] launch start, [1 + f] frame f complete);
+    records_ready: every frame's cull has just prepared its records
+    (NDG_RECORDS_READY)."""
     keep = []
     arr = (FrameC * len(frames))()
+    fl = NDG_RECORDS_READY if records_ready else 0
     for i, (mix, x, tile, cull, y, ws) in enumerate(frames):
         mc, qc, cc = mix.c(), queries_c(x, tile), cull.c()
         keep += [mc, qc, cc]
         arr[i] = FrameC(ctypes.pointer(mc), ctypes.pointer(qc), ctypes.pointer(cc),
-                        y.data_ptr(), ws.data_ptr(), ws.numel())
+                        y.data_ptr(), ws.data_ptr(), ws.numel(), fl)
     _check(lib().ndg_forward_batch(arr, len(frames), _ptr(batch_ws), batch_ws.numel(),
                                    _ptr(stamps) if stamps is not None else None,
                                    _stream(stream), _tr(trace)), "ndg_forward_batch")

@@ -110,4 +110,4 @@ def render_batch(frames, batch_ws: torch.Tensor, stamps: torch.Tensor | None = N
         ev = fr.evaluator(tile)
         ndg.build_cull(fr.mix, fr.x, tile, fr.cp, ev.cull, ev.ws)
         items.append((fr.mix, fr.x, tile, ev.cull, fr.y, ev.ws))
-    ndg.forward_batch(items, batch_ws, stamps, trace=trace)
+    ndg.forward_batch(items, batch_ws, stamps, trace=trace, records_ready=True)

@@ -217,3 +217,7 @@ def test_forward_batch_host_checks(ndg):
         assert L.ndg_forward_batch(frames(good, f2), 2, fake_ws, s64, None, None, None) == E
     assert L.ndg_forward_batch(frames(good, (m, 0x7000, 0x10000, 16)), 2, fake_ws, s64, None,
                                None, None) == ndg.NDG_ERR_WORKSPACE
+    # an unknown frame flag
+    fs = frames(good, good)
+    fs[1].flags = 0x4
+    assert L.ndg_forward_batch(fs, 2, fake_ws, s64, None, None, None) == E

@@ -101,6 +101,16 @@ def test_batch_equals_per_frame_forward_and_oracle(ndg, oracle):
     torch.cuda.synchronize()
     for i, f in enumerate(fr):
         assert torch.equal(f["y"], f["y_ref"]), f"frame {i}: second batch differs"
+    # after fresh culls, reusing the records they prepared (NDG_RECORDS_READY)
+    for f in fr:
+        f["ev"].build(f["gm"])
+        f["y"].fill_(float("nan"))
+    tr2 = ndg.Trace()
+    ndg.forward_batch(items, bws, None, trace=tr2, records_ready=True)
+    torch.cuda.synchronize()
+    assert tr2.launches == 1  # no preparation, the one persistent launch
+    for i, f in enumerate(fr):
+        assert torch.equal(f["y"], f["y_ref"]), f"frame {i}: batch on the cull's records differs"
 
 
 def test_batch_of_one_frame_fills_every_sm(ndg):
