@@ -1,5 +1,6 @@
 // bwd_hb.cu -- the analytic backward on the tensor cores in the beta form
-// (ndg_backward, NDG_MODE_TC, 1 <= N <= 12).
+// (ndg_backward, NDG_MODE_TC, N = 7..12; built for every N <= 12, while
+// N <= 6 dispatches the E Psi form of bwd_h.cu, measured faster there).
 //
 // With the lifted form of the forward (s = phi(x~) . coef, e = 2^s, the
 // coefficients scaled by -log2(e) / 2), the gradients of an entry (Gaussian
